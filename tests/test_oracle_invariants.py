@@ -1,0 +1,317 @@
+"""Pins of the oracle's whole RK-stage path against closed forms and
+invariants: exact metrics on affine grids, periodic metrics, free-stream
+preservation, discrete conservation, multi-block = single block, the
+isentropic vortex's convergence order, RK3's temporal order, viscous decay
+rates and the TGV dissipation rate."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_07964_gb300 import workloads as W
+
+G = 1.4
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _threads():
+    oracle.set_threads(min(8, max(1, oracle.max_threads())))
+
+
+def _single(xyz, q, L, **kw):
+    P = oracle.Problem(gamma=G, **kw)
+    P.add_block(xyz)
+    for f, face in enumerate(W.periodic_faces(L)):
+        P.set_face(0, f, face.kind, face.nbr, face.nbr_face, face.translate)
+    P.check()
+    P.metrics()
+    P.set_state(0, q)
+    return P
+
+
+# ---------------------------------------------------------------- metrics (Eqs. 7-8)
+
+def test_metrics_exact_on_affine_periodic_grid():
+    """x = A X on a periodic lattice: the conservative metrics are the cofactors
+    of the grid Jacobian (h_d A[:, d] columns) and J^-1 is its determinant."""
+    n = (8, 9, 10)
+    L = (1.0, 1.2, 0.9)
+    A = np.array([[1.0, 0.2, -0.1], [0.15, 0.9, 0.05], [-0.05, 0.1, 1.1]])
+    X, Y, Z = W.lattice(n, L)
+    xyz = np.einsum("ab,bkji->akji", A, np.stack([X, Y, Z]))
+    P = oracle.Problem(gamma=G)
+    P.add_block(xyz)
+    for d in range(3):
+        t = A[:, d] * L[d]
+        P.set_face(0, 2 * d, "periodic", 0, 2 * d + 1, tuple(-t))
+        P.set_face(0, 2 * d + 1, "periodic", 0, 2 * d, tuple(t))
+    P.check()
+    P.metrics()
+    m = P.get_metrics(0, padded=True)
+    h = np.array([L[d] / n[d] for d in range(3)])
+    Jm = A * h[None, :]                          # d x / d xi
+    cof = np.linalg.inv(Jm) * np.linalg.det(Jm)  # row d: (xi_d)_(x,y,z) / J
+    for d in range(3):
+        for c in range(3):
+            assert np.allclose(m[3 * d + c], cof[d, c], rtol=1e-12, atol=1e-14)
+    assert np.allclose(m[9], 1.0 / np.linalg.det(Jm), rtol=1e-12)
+
+
+def test_metrics_periodic_across_seams():
+    """Ghost-layer metrics of a warped periodic block equal the metrics of the
+    periodic partner nodes (coordinates carry the translation, metrics do not)."""
+    w = W.vortex(12, amp=0.1)
+    P = oracle.from_workload(w)
+    m = P.get_metrics(0, padded=True)
+    inner = m[:, 3:-3, 3:-3, 3:-3]
+    assert np.allclose(m[:, 3:-3, 3:-3, :3], inner[:, :, :, -3:], rtol=1e-12, atol=1e-13)
+    assert np.allclose(m[:, 3:-3, :3, 3:-3], inner[:, :, -3:, :], rtol=1e-12, atol=1e-13)
+    assert np.allclose(m[:, -3:, 3:-3, 3:-3], inner[:, :3, :, :], rtol=1e-12, atol=1e-13)
+
+
+def test_metric_identity_warped():
+    """Sum_d D_d(m^_d) = 0 at every node (the geometric conservation law that
+    Eq. (7) is built for), with D the sixth-order central operator."""
+    w = W.vortex(12, amp=0.1)
+    P = oracle.from_workload(w)
+    m = P.get_metrics(0, padded=True)
+    a = (0.75, -0.15, 1.0 / 60.0)
+    for c in range(3):
+        s = np.zeros_like(m[0, 3:-3, 3:-3, 3:-3])
+        for d, ax in ((0, 2), (1, 1), (2, 0)):
+            f = m[3 * d + c]
+            for k, ak in enumerate(a, start=1):
+                sl_p = [slice(3, -3)] * 3
+                sl_m = [slice(3, -3)] * 3
+                n = f.shape[ax]
+                sl_p[ax] = slice(3 + k, n - 3 + k)
+                sl_m[ax] = slice(3 - k, n - 3 - k)
+                s += ak * (f[tuple(sl_p)] - f[tuple(sl_m)])
+        assert np.abs(s).max() < 1e-12 * np.abs(m[c]).max()
+
+
+# ---------------------------------------------------------------- free stream, conservation
+
+def test_free_stream_preserved_on_warped_grid():
+    """Uniform flow on the warped periodic 32^3 grid: R at round-off, and the
+    state stays uniform over 10 RK3 steps."""
+    w = W.vortex(32, free_stream=True)
+    P = oracle.from_workload(w)
+    P.rhs()
+    r = P.get_rhs(0)
+    q0 = w.blocks[0].q0
+    assert np.abs(r).max() < 1e-12
+    dt, _ = P.dt(0.5)
+    P.step(10, dt)
+    assert np.abs(P.get_state(0) - q0).max() < 1e-12
+
+
+def test_free_stream_preserved_navier_stokes_multiblock():
+    w = W.vortex(16, free_stream=True)
+    blocks = W.split_periodic_box(w.blocks[0].xyz, w.meta["L"], (2, 1, 2))
+    P = oracle.Problem(gamma=G, mach=0.5, reynolds=100.0, viscous=True)
+    for b in blocks:
+        P.add_block(b.xyz)
+    for bi, b in enumerate(blocks):
+        for f, face in enumerate(b.faces):
+            P.set_face(bi, f, face.kind, face.nbr, face.nbr_face, face.translate)
+    P.check()
+    P.metrics()
+    for bi, qb in enumerate(W.split_state(w.blocks[0].q0, (2, 1, 2))):
+        P.set_state(bi, qb)
+    P.rhs()
+    for bi in range(len(blocks)):
+        assert np.abs(P.get_rhs(bi)).max() < 1e-12
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_discrete_conservation_periodic(viscous):
+    """Sum of Q/J over a periodic block is constant (Eq. (19) and the viscous
+    central differences telescope)."""
+    w = W.tgv(16) if viscous else W.vortex(16)
+    w.reynolds = 50.0
+    P = oracle.from_workload(w)
+    J = P.get_metrics(0)[9]
+    tot0 = (w.blocks[0].q0 / J).sum(axis=(1, 2, 3))
+    dt, _ = P.dt(0.5)
+    P.step(3, dt)
+    tot = (P.get_state(0) / J).sum(axis=(1, 2, 3))
+    scale = np.abs(w.blocks[0].q0 / J).sum(axis=(1, 2, 3)).max()
+    assert np.abs(tot - tot0).max() < 1e-13 * scale
+
+
+# ---------------------------------------------------------------- topology
+
+@pytest.mark.parametrize("parts", [(2, 1, 1), (2, 2, 1), (1, 3, 2)])
+def test_split_box_equals_single_block(parts):
+    w = W.vortex(18, amp=0.1)
+    w.viscous = True
+    w.reynolds = 200.0
+    single = oracle.from_workload(w)
+    dt, _ = single.dt(0.5)
+    single.step(2, dt)
+    qs = single.get_state(0)
+    blocks = W.split_periodic_box(w.blocks[0].xyz, w.meta["L"], parts)
+    P = oracle.Problem(gamma=G, mach=0.5, reynolds=200.0, viscous=True)
+    for b in blocks:
+        P.add_block(b.xyz)
+    for bi, b in enumerate(blocks):
+        for f, face in enumerate(b.faces):
+            P.set_face(bi, f, face.kind, face.nbr, face.nbr_face, face.translate)
+    P.check()
+    P.metrics()
+    parts_q = W.split_state(w.blocks[0].q0, parts)
+    for bi, qb in enumerate(parts_q):
+        P.set_state(bi, qb)
+    P.step(2, dt)
+    ref = W.split_state(qs, parts)
+    for bi in range(len(blocks)):
+        assert np.abs(P.get_state(bi) - ref[bi]).max() < 1e-13
+
+
+def test_topology_check_rejects_mismatch():
+    w = W.vortex(8)
+    P = oracle.Problem(gamma=G)
+    P.add_block(w.blocks[0].xyz)
+    for f in range(6):
+        P.set_face(0, f, "periodic", 0, f, (0, 0, 0))   # wrong partner face
+    with pytest.raises(ValueError):
+        P.check()
+
+
+# ---------------------------------------------------------------- time step (reading R8)
+
+def test_dt_closed_form_on_uniform_lattice():
+    n, L = 12, 3.0
+    X, Y, Z = W.lattice((n, n, n), (L, L, L))
+    xyz = np.stack([X, Y, Z])
+    q = W.conservative(G, np.ones_like(X), 0.3, -0.2, 0.1, 1.0 / G)
+    P = _single(xyz, q, (L, L, L))
+    h = L / n
+    dt, _ = P.dt(0.5)
+    assert dt == pytest.approx(0.5 * h / (0.3 + 0.2 + 0.1 + 3.0), rel=1e-12)
+
+
+# ---------------------------------------------------------------- accuracy
+
+def _vortex_error(n, T, cfl_ref=None, amp=0.05):
+    w = W.vortex(n, dims=2, nk=6, amp=amp)
+    P = oracle.from_workload(w)
+    g, _ = P.dt(0.5)
+    return P, w, g
+
+
+@pytest.mark.slow
+def test_vortex_convergence_order():
+    """Isentropic vortex on a warped grid against the exact translated vortex:
+    with dt ~ dx^(5/3), the error falls at (close to) fifth order."""
+    T = 0.6
+    c = None
+    errs = []
+    for n in (32, 64, 128):
+        w = W.vortex(n, dims=2, nk=6, amp=0.05)
+        P = oracle.from_workload(w)
+        g, _ = P.dt(0.5)
+        if c is None:
+            c = g / (10.0 / n) ** (5.0 / 3.0)
+        ns = int(np.ceil(T / (c * (10.0 / n) ** (5.0 / 3.0))))
+        P.step(ns, T / ns)
+        xyz = w.blocks[0].xyz
+        ex = W.conservative(G, *W.isentropic_vortex(G, xyz[0], xyz[1], t=T))
+        errs.append(np.sqrt(((P.get_state(0) - ex) ** 2).mean()))
+    order = np.log2(errs[1] / errs[2])
+    assert order > 4.3, errs
+    assert errs[2] < 1e-5
+
+
+def test_vortex_c1_translation_error():
+    """32^3 warped vortex, 10 steps at CFL 0.5: close to the exact solution."""
+    w = W.vortex(32)
+    P = oracle.from_workload(w)
+    dt, _ = P.dt(0.5)
+    P.step(10, dt)
+    xyz = w.blocks[0].xyz
+    ex = W.conservative(G, *W.isentropic_vortex(G, xyz[0], xyz[1], t=10 * dt))
+    err = np.abs(P.get_state(0) - ex).max(axis=(1, 2, 3))
+    assert err.max() < 0.05
+    assert np.abs(P.get_state(0) - w.blocks[0].q0).max() > 0.05   # the vortex moved
+
+
+def test_rk3_third_order_in_time():
+    """Eq. (20): halving dt on a fixed grid cuts the temporal error by ~8."""
+    sols = []
+    T = 0.4
+    for ns in (4, 8, 16):
+        w = W.vortex(16, dims=2, nk=6, amp=0.05)
+        P = oracle.from_workload(w)
+        P.step(ns, T / ns)
+        sols.append(P.get_state(0))
+    e1 = np.abs(sols[0] - sols[2]).max()
+    e2 = np.abs(sols[1] - sols[2]).max()
+    # Richardson: (e1)/(e2) = (1 - 2^-3*... ) -> ratio 9 for exact order 3
+    assert 7.0 < e1 / e2 < 11.0
+
+
+# ---------------------------------------------------------------- viscous closed forms
+
+def test_shear_wave_decay_rate():
+    """u = A sin(y), rho = 1, p uniform: the Euler terms vanish and the
+    amplitude decays as exp(-nu t) with nu = (Ma/Re) mu / rho (mu = 1)."""
+    n = 16
+    L = 2 * np.pi
+    xyz = W.warped_box((n, n, n), (L, L, L), 0.02)
+    A = 1e-3
+    u = A * np.sin(xyz[1])
+    q = W.conservative(G, np.ones_like(u), u, 0.0, 0.0, 1.0 / G)
+    mach, re = 0.5, 5.0
+    P = _single(xyz, q, (L, L, L), mach=mach, reynolds=re, viscous=True, mu_law=0)
+    nu = mach / re
+    T, ns = 1.0, 20
+    P.step(ns, T / ns)
+    qq = P.get_state(0)
+    amp = (qq[1] * np.sin(xyz[1])).sum() / (np.sin(xyz[1]) ** 2).sum()
+    assert amp / A == pytest.approx(np.exp(-nu * T), rel=2e-3)
+
+
+def test_heat_conduction_decay_rate():
+    """Entropy wave T = 1 + A sin(y) at uniform p, at rest: in the isobaric
+    limit T decays as exp(-alpha t), alpha = (Ma/Re) mu/(Pr rho) (c_p = 1/(gamma-1))."""
+    n = 16
+    L = 2 * np.pi
+    X, Y, Z = W.lattice((n, n, n), (L, L, L))
+    xyz = np.stack([X, Y, Z])
+    A = 1e-3
+    T0 = 1.0 + A * np.sin(Y)
+    p = 1.0 / G
+    rho = G * p / T0
+    q = W.conservative(G, rho, 0.0, 0.0, 0.0, p)
+    mach, re, pr = 0.02, 1.0, 0.7
+    P = _single(xyz, q, (L, L, L), mach=mach, reynolds=re, prandtl=pr, viscous=True, mu_law=0)
+    alpha = mach / re / pr
+    Tend, ns = 10.0, 60
+    P.step(ns, Tend / ns)
+    qq = P.get_state(0)
+    rr, uu, vv, ww, pp = W.primitive(G, qq)
+    TT = G * pp / rr
+    amp = ((TT - 1.0) * np.sin(Y)).sum() / (np.sin(Y) ** 2).sum()
+    assert amp / A == pytest.approx(np.exp(-alpha * Tend), rel=0.02)
+
+
+def test_tgv_viscous_dissipation_rate():
+    """Taylor-Green vortex at t = 0: the viscous part of dK/dt equals
+    -2 nu |k|^2 K = -6 nu K for its |k|^2 = 3 modes (within the Ma = 0.1
+    compressibility), nu = (Ma/Re) mu (mu = 1, rho ~ 1)."""
+    w = W.tgv(24, mu_law=0)
+    out = []
+    for visc in (True, False):
+        w.viscous = visc
+        P = oracle.from_workload(w)
+        P.rhs()
+        out.append(P.get_rhs(0))
+        J = P.get_metrics(0)[9]
+    q = w.blocks[0].q0
+    rho, u, v, ww, p = W.primitive(G, q)
+    K = (0.5 * rho * (u * u + v * v + ww * ww) / J).sum()
+    dR = out[0] - out[1]
+    dK = ((u * dR[1] + v * dR[2] + ww * dR[3] - 0.5 * (u * u + v * v + ww * ww) * dR[0]) / J).sum()
+    nu = w.mach / w.reynolds
+    assert -dK / K == pytest.approx(6 * nu, rel=0.02)
