@@ -130,12 +130,21 @@ static double mid6(const double *f /* f[0] = node i */) {
 
 /* Eq. (17): smoothness indicators of the three 3-node sub-stencils of the
  * 5-node stencil W[0..4] = W_{i-2..i+2}; b[0] on {i-2,i-1,i}, b[1] on
- * {i-1,i,i+1}, b[2] on {i,i+1,i+2}. */
+ * {i-1,i,i+1}, b[2] on {i,i+1,i+2}.  Eq. (17) defines each indicator as the
+ * scaled sum of the squared L2 norms of the derivatives of the sub-stencil's
+ * interpolation polynomial; that sum is written out here term by term,
+ * (13/12) (second difference)^2 + (1/4) (first derivative at the node)^2,
+ * which equals the printed quadratic form exactly but without its
+ * cancellation (the expanded form loses ~1e-16 W^2 absolutely, a large
+ * perturbation next to epsilon = 1e-6 of Eq. (15)). */
 static void weno_beta(const double *W, double b[3]) {
     const double a = W[0], c = W[1], d = W[2], e = W[3], g = W[4];
-    b[0] = (4.0 * a * a - 19.0 * a * c + 25.0 * c * c + 11.0 * a * d - 31.0 * c * d + 10.0 * d * d) / 3.0;
-    b[1] = (4.0 * c * c - 13.0 * c * d + 13.0 * d * d + 5.0 * c * e - 13.0 * d * e + 4.0 * e * e) / 3.0;
-    b[2] = (10.0 * d * d - 31.0 * d * e + 25.0 * e * e + 11.0 * d * g - 19.0 * e * g + 4.0 * g * g) / 3.0;
+    const double s1 = a - 2.0 * c + d, t1 = a - 4.0 * c + 3.0 * d;
+    const double s2 = c - 2.0 * d + e, t2 = c - e;
+    const double s3 = d - 2.0 * e + g, t3 = 3.0 * d - 4.0 * e + g;
+    b[0] = 13.0 / 12.0 * s1 * s1 + 1.0 / 4.0 * t1 * t1;
+    b[1] = 13.0 / 12.0 * s2 * s2 + 1.0 / 4.0 * t2 * t2;
+    b[2] = 13.0 / 12.0 * s3 * s3 + 1.0 / 4.0 * t3 * t3;
 }
 
 static const double WENO_EPS = 1.0e-6;   /* Eq. (15) epsilon */

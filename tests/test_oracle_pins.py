@@ -103,16 +103,30 @@ def test_weno_paper_literal_pairing_is_not_fifth_order():
     assert [lit[s] * 128 for s in range(-2, 3)] != [3, -20, 90, 60, -5]
 
 
-def test_weno_beta_equals_jiang_shu_form():
-    """Eq. (17) equals 13/12 (second difference)^2 + 1/4 (one-sided first difference)^2."""
+def test_weno_beta_equals_printed_eq17():
+    """The oracle's indicators equal the printed quadratic forms of Eq. (17),
+    evaluated exactly in rational arithmetic on the same (binary) inputs."""
+    cf = coefficients()
     for _ in range(50):
         W = RNG.normal(size=5)
         b, _, _ = oracle.op_weno(W)
-        a, c, d, e, g = W
-        js = [13 / 12 * (a - 2 * c + d) ** 2 + 0.25 * (a - 4 * c + 3 * d) ** 2,
-              13 / 12 * (c - 2 * d + e) ** 2 + 0.25 * (c - e) ** 2,
-              13 / 12 * (d - 2 * e + g) ** 2 + 0.25 * (3 * d - 4 * e + g) ** 2]
-        assert np.allclose(b, js, rtol=1e-12, atol=1e-13)
+        Wf = [Fraction(float(x)) for x in W]
+        for j, name in enumerate(("eq17_b1", "eq17_b2", "eq17_b3")):
+            exact = sum(c * Wf[k // 10] * Wf[k % 10] for k, c in cf[name].items()) / 3
+            assert abs(Fraction(b[j]) - exact) <= Fraction(1, 10 ** 14) * max(abs(exact), Fraction(1, 10 ** 6))
+
+
+def test_weno_beta_is_well_conditioned():
+    """Smooth data around a large offset: the indicators keep their relative
+    accuracy (no cancellation of the O(W^2) terms)."""
+    x = np.arange(-2, 3) * 1e-3
+    W = 5.0 + x + 0.5 * x * x
+    b, _, _ = oracle.op_weno(W)
+    Wf = [Fraction(float(v)) for v in W]
+    cf = coefficients()
+    for j, name in enumerate(("eq17_b1", "eq17_b2", "eq17_b3")):
+        exact = sum(c * Wf[k // 10] * Wf[k % 10] for k, c in cf[name].items()) / 3
+        assert abs(Fraction(b[j]) - exact) <= Fraction(1, 10 ** 12) * abs(exact)
 
 
 def test_weno_exact_on_linear_data():
