@@ -1,0 +1,330 @@
+"""Benchmark: grid-point RK-stage updates per second of the residual path.
+
+Default workload (N = 1): the 3D Taylor-Green vortex, compressible
+Navier-Stokes at Re 1600, Ma 0.1, Pr 0.71, on one periodic 128^3 block with a
+0.02 L sinusoidal warp -- FP64 state and metrics, SSP-RK3.  The line's
+``value`` is the FP64 form; ``mixed`` carries the same workload in the mixed
+FP32/FP64 form and the ratio.  A "step" is one full RK3 step (three stages)
+over the block; value = nodes * 3 * steps / device time (Mpts/s).
+
+--impl reference times the FP64 CPU oracle (as it stands) on this host's
+cores on the same workload instead.  Under torchrun (N > 1) each rank runs an
+independent replica on its own GPU (the path keeps every block on one GPU).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point RK-stage updates/s (Mpts/s) mixed vs FP64 on 1 GB300; HBM GB/s fraction"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 / FP32 SIMT peaks derived from the GB300's unit counts and max clock:
+# FP64 1.25 TFLOP/s (nominal); FP32 152 SMs x 128 lanes x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# Algorithmic work of one flux-sweep launch per interior node (one direction):
+# modified AFWENO inviscid part and, for Navier-Stokes, the viscous node flux
+# and its central derivative (counts derived operation by operation).
+FLUX_FLOPS_INV = 1060
+FLUX_FLOPS_VISC = 85
+
+
+def flux_bytes_per_node(dir_, word, viscous):
+    """Compulsory HBM bytes per node of one flux-sweep launch: the state (5),
+    the metric of the direction (3), the accumulator (written by the xi sweep,
+    read and written by eta, zeta) and, for Navier-Stokes, primitives (4) and
+    gradients (12)."""
+    words = 5 + 3 + (5 if dir_ == 0 else 10) + (16 if viscous else 0)
+    return words * word
+
+
+WORKLOADS = {
+    "tgv128": ("Taylor-Green vortex, NS Re1600 Ma0.1 Pr0.71, warped periodic 128^3 block", lambda W: W.tgv(128)),
+    "tgv256": ("Taylor-Green vortex, NS Re1600 Ma0.1 Pr0.71, warped periodic 256^3 block", lambda W: W.tgv(256)),
+    "tgv384": ("Taylor-Green vortex, NS Re1600 Ma0.1 Pr0.71, warped periodic 384^3 block", lambda W: W.tgv(384)),
+    "vortex32": ("isentropic vortex, Euler, warped periodic 32^3 block", lambda W: W.vortex(32)),
+    "ogrid": ("cylinder O-grid, NS Ma0.2 Re3900, 8 blocks, 3,538,944 nodes", lambda W: W.ogrid()),
+    "batch64": ("64 isentropic-vortex instances, edges from {24..96}, seeded", lambda W: W.batch(64)),
+}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "src": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": PEAKS_FALLBACK["hbm_gbs"], "src": "fallback"}
+
+
+def pinned_like(torch, a):
+    t = torch.empty(a.shape, dtype=torch.float64).pin_memory()
+    t.numpy()[...] = a
+    return t
+
+
+def run_form(torch, hx, w, precision, steps, warmup, stream, dt):
+    """Times `steps` graph-replayed RK3 steps with CUDA events on the
+    context's stream; returns (seconds, ctx)."""
+    ctx = hx.from_workload(w, precision=precision, stream=stream.cuda_stream)
+    ctx.step(warmup, dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(steps, dt)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3, ctx
+
+
+def roofline_for(ctx, w, precision, steps, dt, peaks):
+    """Per-kernel CUDA-event durations of `steps` launch-by-launch steps of
+    the same workload on the same stream; roofline of the dominant kernel."""
+    stats = ctx.profile_step(steps, dt)
+    name, (launches, tot) = max(stats.items(), key=lambda kv: kv[1][1])
+    per_launch_s = tot / launches / 1e3
+    npts = w.npts
+    out = {"kernel": name, "launch_ms": tot / launches, "share": tot / sum(v[1] for v in stats.values())}
+    if name.startswith("flux_"):
+        d = {"flux_xi": 0, "flux_eta": 1, "flux_zeta": 2}[name]
+        word = 8 if precision == "fp64" else 4
+        flops = (FLUX_FLOPS_INV + (FLUX_FLOPS_VISC if w.viscous else 0)) * npts
+        bytes_ = flux_bytes_per_node(d, word, w.viscous) * npts
+        gbs = bytes_ / per_launch_s / 1e9
+        tfl = flops / per_launch_s / 1e12
+        alu_peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+        hbm_frac = gbs / peaks["hbm_gbs"]
+        alu_frac = tfl / alu_peak
+        if precision == "fp64" or alu_frac >= hbm_frac:
+            out.update({"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
+                        "peak_src": "derived (FP64 1.25 TFLOP/s nominal)" if precision == "fp64"
+                        else "derived (152 SM x 128 FP32 lanes x 2 x 2.07 GHz)",
+                        "hbm_view": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac}})
+        else:
+            out.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
+                        "peak_src": peaks["src"],
+                        "alu_view": {"achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac}})
+    out["traffic"] = None
+    out["per_kernel_ms"] = {k: v[1] / v[0] for k, v in stats.items()}
+    return out
+
+
+def cpu_baseline(w, seconds_target=15.0):
+    """The FP64 oracle as it stands on this host's cores: whole RK3 steps of
+    the same workload until about `seconds_target` of CPU time."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    P = oracle.from_workload(w)
+    dt, _ = P.dt(0.5)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        P.step(1, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_target or steps >= 50:
+            break
+    return {"value": w.npts * 3 * steps / el / 1e6, "unit": "Mpts/s", "cores": oracle.max_threads(),
+            "kind": "oracle", "sample": "%d full RK3 step(s) of the %d-node workload, %.1f s" % (steps, w.npts, el)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tgv128", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--forms", default="fp64,mixed", help="comma list of fp64, mixed")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    forms = [f for f in args.forms.split(",") if f]
+    if args.no_mixed and "mixed" in forms:
+        forms.remove("mixed")
+    if not forms or any(f not in ("fp64", "mixed") for f in forms):
+        ap.error("--forms takes fp64 and/or mixed")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2006_07964_gb300 import workloads as W
+    desc, make = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        w = make(W)
+        threads = os.cpu_count() or 1
+        oracle.set_threads(threads)
+        P = oracle.from_workload(w)
+        dt, _ = P.dt(0.5)
+        P.step(min(args.warmup, 1), dt)
+        t0 = time.perf_counter()
+        P.step(args.steps, dt)
+        el = time.perf_counter() - t0
+        v = w.npts * 3 * args.steps / el / 1e6
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpts/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": args.workload + ": " + desc, "points": w.npts},
+                "cpu_baseline": {"value": v, "unit": "Mpts/s", "cores": oracle.max_threads(), "kind": "oracle",
+                                 "sample": "%d full RK3 steps of the whole workload" % args.steps},
+                "e2e": {"value": v, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_2006_07964_gb300 import build, hx
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    w = make(W)
+    stream = torch.cuda.Stream()
+    peaks = load_peaks()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # time step from the FP64 state (held fixed, as the oracle does)
+    probe = hx.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+    dt, _ = probe.compute_dt(0.5)
+    probe.close()
+
+    # headline form first (fp64 unless only mixed is asked for), clocks sampled
+    # during its timed region
+    head = forms[0]
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    secs, ctx = run_form(torch, hx, w, head, args.steps, args.warmup, stream, dt)
+    ck = clocks.stop()
+    barrier()
+    secs = max_over_ranks(secs)
+    launches = ctx.launches_per_step * args.steps
+    value = world * w.npts * 3 * args.steps / secs / 1e6
+    roof = roofline_for(ctx, w, head, 2, dt, peaks)
+    ctx.close()
+
+    mixed = None
+    if head == "fp64" and "mixed" in forms:
+        msecs, mctx = run_form(torch, hx, w, "mixed", args.steps, args.warmup, stream, dt)
+        msecs = max_over_ranks(msecs)
+        mval = world * w.npts * 3 * args.steps / msecs / 1e6
+        mixed = {"value": mval, "ms_per_step": msecs / args.steps * 1e3, "ratio_vs_fp64": mval / value,
+                 "dtype": "f32 state/fluxes/WENO, f64 metrics/RK", "gpu_launches": mctx.launches_per_step * args.steps,
+                 "roofline": roofline_for(mctx, w, "mixed", 2, dt, peaks)}
+        mctx.close()
+
+    # end to end through the C ABI with host (pinned) buffers: per step the
+    # state goes host -> device, one RK3 step runs, the state comes back
+    ectx = hx.from_workload(w, precision=head, stream=stream.cuda_stream)
+    hq = [pinned_like(torch, b.q0) for b in w.blocks]
+    hout = [torch.empty(b.q0.shape, dtype=torch.float64).pin_memory() for b in w.blocks]
+    h2d = sum(b.q0.nbytes for b in w.blocks)
+    e_steps = max(3, min(args.steps, 10))
+    for b in range(len(w.blocks)):
+        ectx.set_state(b, hq[b].numpy())
+    ectx.step(1, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        for b in range(len(w.blocks)):
+            ectx.set_state(b, hq[b].numpy())
+        ectx.step(1, dt)
+        for b in range(len(w.blocks)):
+            ectx.get_state(b, hout[b].numpy())
+    e_secs = max_over_ranks(time.perf_counter() - t0)
+    ectx.close()
+    e2e = {"value": world * w.npts * 3 * e_steps / e_secs / 1e6, "unit": "Mpts/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": h2d, "steps": e_steps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "f32 state/fluxes/WENO, f64 metrics/RK", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + desc, "points": w.npts, "blocks": len(w.blocks),
+                   "dt": dt, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (resident state and metrics %.0f MB per replica)"
+                         % (w.npts * (10 + 15) * 8 / 1e6)},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+        "mixed": mixed,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

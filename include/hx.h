@@ -1,0 +1,182 @@
+/*
+ * hx.h -- C ABI of the GB300 (sm_103a) library for the per-Runge-Kutta-stage
+ * residual evaluation and update of a multi-block curvilinear high-order
+ * finite-difference compressible Navier-Stokes solver, after Ye, Zhang, Wan,
+ * Yan, Sun, "Accelerating CFD simulation with high order finite difference
+ * method on curvilinear coordinates for modern GPU clusters" (HiResX).
+ *
+ * Method (section / equation of the paper):
+ *   - nondimensional Navier-Stokes in curvilinear form, Eqs. (1)-(6);
+ *   - conservative metrics and Jacobian, Eqs. (7)-(8), sixth-order central
+ *     differences (Sec. 2);
+ *   - inviscid fluxes by the modified alternative-formulation WENO5
+ *     (characteristic space at the node, shared smoothness indicators,
+ *     Sec. 4.5.1, Figs. 10-11) with Steger-Warming splitting, Eqs. (9)-(19);
+ *   - viscous fluxes at nodes from chain-rule gradients, Eq. (21), and their
+ *     sixth-order central divergence (Sec. 4.5.2, Fig. 12);
+ *   - R = -J * sum_d d/d(xi_d)(E_d - E_v,d), Eqs. (2)-(3);
+ *   - TVD Runge-Kutta 3, Eq. (20);
+ *   - on-device block-interface and physical-boundary halo fill (Fig. 2:
+ *     bc_block, bc_phys; Sec. 4.1: blocks of one process exchanged on the GPU).
+ *
+ * Conventions for every entry point:
+ *   - returns HX_OK (0) on success or a negative HX_ERR_* code; the message
+ *     of the last failure of a context is available from hx_last_error();
+ *   - arrays are C-contiguous double precision in the layouts stated below,
+ *     i fastest: a block field is [nk][nj][ni];
+ *   - the library copies every input; callers keep ownership of their
+ *     buffers and may free them when the call returns;
+ *   - pointers flagged "on_device" are CUDA device pointers on the device
+ *     current when hx_create was called (e.g. torch tensors); otherwise they
+ *     are host pointers (pinned memory makes the copies faster);
+ *   - calls on one context are not thread-safe; work is issued on the
+ *     context's stream and every call returns after that stream is idle.
+ * There is no CPU fallback: without a CUDA device hx_create fails with
+ * HX_ERR_CUDA.
+ */
+#ifndef HX_H
+#define HX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HX_OK = 0,
+    HX_ERR_INVALID_ARG = -1,  /* bad pointer, index, size or value              */
+    HX_ERR_STATE = -2,        /* call out of order (e.g. step before metrics)    */
+    HX_ERR_TOPOLOGY = -3,     /* unset face, unmatched or inconsistent neighbour */
+    HX_ERR_BAD_GRID = -4,     /* a node has J^-1 <= 0 (Eq. (8))                  */
+    HX_ERR_OOM = -5,          /* device allocation failed or cap exceeded        */
+    HX_ERR_CUDA = -6,         /* a CUDA runtime call failed                      */
+    HX_ERR_NONFINITE = -7,    /* a step produced a non-finite state              */
+    HX_ERR_UNPHYSICAL = -8,   /* non-positive density or pressure after a step   */
+    HX_ERR_TIMEOUT = -9       /* reserved: a bounded device wait gave up         */
+};
+
+/* Face kinds (Sec. 4.2: connecting faces and physical faces). */
+enum {
+    HX_FACE_PERIODIC = 0,   /* joined to a face of the same or another block, coordinates translated */
+    HX_FACE_INTERFACE = 1,  /* 1:1 block interface, node-disjoint continuation                       */
+    HX_FACE_WALL = 2,       /* no-slip adiabatic wall on the boundary nodes                          */
+    HX_FACE_FARFIELD = 3    /* characteristic far field (1D Riemann invariants)                      */
+};
+
+enum { HX_FP64 = 0, HX_MIXED = 1 };
+
+typedef struct {
+    double gamma;         /* specific heat ratio (1.4)                                 */
+    double mach;          /* free-stream Mach number Ma (free stream along +x)         */
+    double reynolds;      /* free-stream Reynolds number Re                             */
+    double prandtl;       /* Prandtl number Pr                                          */
+    int viscous;          /* 0: Euler, 1: Navier-Stokes                                 */
+    int mu_law;           /* 0: mu = 1, 1: Sutherland mu = T^1.5 (1+S)/(T+S)            */
+    double sutherland_s;  /* S of Sutherland's law (110.4/288.15)                       */
+    int precision;        /* HX_FP64, or HX_MIXED: FP32 state, fluxes and WENO with FP32
+                             accumulation; FP64 metrics, Jacobian and RK combination    */
+    int scheme;           /* 0: modified AFWENO (the only scheme built)                 */
+    size_t mem_cap_bytes; /* 0: no cap; else hx_finalize fails with HX_ERR_OOM above it */
+    int autotune;         /* 1: time the tile-shape candidates once per shape class     */
+} hx_config;
+
+typedef struct hx_ctx hx_ctx;
+
+/* Per-kernel-family timing of hx_profile_step. */
+typedef struct {
+    char name[32];
+    int launches;         /* launches in the profiled steps              */
+    double total_ms;      /* summed CUDA-event durations                 */
+} hx_kernel_stat;
+
+/* Fills cfg with gamma 1.4, Ma 0.5, Re 1, Pr 0.72, Euler, Sutherland S,
+ * FP64, modified AFWENO, no cap, autotune on. */
+int hx_config_default(hx_config* cfg);
+
+/* Creates a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t to issue all work on, or NULL for a stream the context
+ * creates and owns. */
+int hx_create(hx_ctx** out, const hx_config* cfg, void* cuda_stream);
+
+/* Adds a block of ni x nj x nk nodes (each >= 6).  xyz is a host array
+ * [3][nk][nj][ni] of node coordinates (x, y, z), copied.  The block id is
+ * written to *block_id (ids are 0, 1, 2, ... in call order). */
+int hx_add_block(hx_ctx* ctx, int ni, int nj, int nk, const double* xyz, int* block_id);
+
+/* Sets face `face` (0..5 = i-, i+, j-, j+, k-, k+) of `block`.  For
+ * PERIODIC and INTERFACE faces, nbr_block/nbr_face name the joined face,
+ * which must be the opposite face of the same direction (i+ joins i-) with
+ * equal extents across; translate (may be NULL = 0) is added to the
+ * neighbour's coordinates to give this block's ghost coordinates.  For WALL
+ * and FARFIELD the neighbour arguments are ignored. */
+int hx_set_face(hx_ctx* ctx, int block, int face, int kind, int nbr_block, int nbr_face,
+                const double translate[3]);
+
+/* Validates the topology (HX_ERR_TOPOLOGY), plans device buffers and work
+ * lists and allocates them (HX_ERR_OOM). */
+int hx_finalize(hx_ctx* ctx);
+
+/* Conservative metrics (Eq. (7)) and Jacobian (Eq. (8)) on every node and on
+ * three ghost layers, in FP64.  Fails with HX_ERR_BAD_GRID if any J^-1 <= 0. */
+int hx_compute_metrics(hx_ctx* ctx);
+
+/* Sets the conservative state (rho, rho u, rho v, rho w, e) of `block` from
+ * q [5][nk][nj][ni]. */
+int hx_set_state(hx_ctx* ctx, int block, const double* q, int on_device);
+
+/* Copies the conservative state of `block` into q_out [5][nk][nj][ni]. */
+int hx_get_state(hx_ctx* ctx, int block, double* q_out, int on_device);
+
+/* Copies the node metrics of `block` into m_out [10][nk][nj][ni]:
+ * xi^_x, xi^_y, xi^_z, eta^_x, ..., zeta^_z (metric / J) and J. */
+int hx_get_metrics(hx_ctx* ctx, int block, double* m_out, int on_device);
+
+/* Time step from the current state:
+ *   dt_b = cfl / max over the nodes of block b of sum_d (|m_d.u| + c |m_d|) J.
+ * dt_global (may be NULL) gets min_b dt_b; dt_per_block (may be NULL) gets
+ * one value per block. */
+int hx_compute_dt(hx_ctx* ctx, double cfl, double* dt_global, double* dt_per_block);
+
+/* Advances every block nsteps TVD-RK3 steps (Eq. (20)) with time step dt.
+ * The step is captured once in a CUDA graph and replayed.  Returns
+ * HX_ERR_NONFINITE if a non-finite value appeared. */
+int hx_step(hx_ctx* ctx, int nsteps, double dt);
+
+/* As hx_step with one time step per block (independent instances). */
+int hx_step_multi(hx_ctx* ctx, int nsteps, const double* dt_per_block);
+
+/* Evaluates R(Q) = dQ/dt of the current state without advancing it and
+ * copies block `block`'s residual into r_out [5][nk][nj][ni]. */
+int hx_rhs(hx_ctx* ctx, int block, double* r_out, int on_device);
+
+/* After hx_rhs of a viscous context: copies the 12 node gradients
+ * (u, v, w, T)_(x, y, z) of `block` into g_out [12][nk][nj][ni]. */
+int hx_get_gradients(hx_ctx* ctx, int block, double* g_out, int on_device);
+
+/* Runs nsteps steps launch by launch (no graph) with CUDA events around each
+ * kernel on the context's stream and reports per-family totals in
+ * out[0..*n_kinds-1] (at most max_kinds).  The state advances as in hx_step. */
+int hx_profile_step(hx_ctx* ctx, int nsteps, double dt, hx_kernel_stat* out, int max_kinds, int* n_kinds);
+
+/* Kernel launches one RK step makes (all stages). */
+int hx_launches_per_step(const hx_ctx* ctx);
+
+/* Total interior nodes over all blocks. */
+long long hx_points(const hx_ctx* ctx);
+
+/* Device bytes held by the context. */
+size_t hx_device_bytes(const hx_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the last hx_create failure when
+ * ctx is NULL).  Valid until the next call on ctx. */
+const char* hx_last_error(const hx_ctx* ctx);
+
+/* Releases every device and host resource of ctx (NULL is allowed). */
+void hx_destroy(hx_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HX_H */

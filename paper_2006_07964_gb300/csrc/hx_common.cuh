@@ -1,0 +1,325 @@
+// hx_common.cuh -- device layout, block table and the per-node arithmetic of
+// the RK-stage residual (Ye et al., HiResX), templated on the working real
+// type R (double for the FP64 form, float for the mixed form).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hx {
+
+// ---------------------------------------------------------------------------
+// layout
+// ---------------------------------------------------------------------------
+// Every block-resident field lives in one arena per buffer: field f of block
+// b, node (i, j, k) is element  f * fstride + base_b + i + j * sj_b + k * sk_b.
+// State-like fields carry G = 3 ghost layers per face (the reach of the
+// six-point stencils of Eqs. (18)-(19)); node coordinates carry GC = 6 (inner
+// and outer derivative of Eq. (7)).  Rows are padded so that i = 0 of every
+// row sits at an 8-element boundary.
+constexpr int G = 3;
+constexpr int GC = 6;
+constexpr int XOFF = 8;
+
+struct DevBlock {
+    int n[3];         // interior nodes per direction
+    int sj, sk;       // element strides of the state layout (si = 1)
+    long long base;   // element index of node (0, 0, 0) in the state layout
+    int phys;         // bit f: face f is a physical face (wall or far field)
+    int wall;         // bit f: face f is a wall
+    double dt;        // time step of this block
+};
+
+struct Gas {
+    double gamma, mach, re, pr, suth;
+    int viscous, mu_law;
+};
+
+struct Tile {          // origin of a sweep tile (node indices)
+    int b, i0, j0, k0;
+};
+
+struct Brick {         // box [i0, i0+ni) x [j0, j0+nj) x [k0, k0+nk) of block b
+    int b, i0, j0, k0, ni, nj, nk, pad;
+};
+
+struct HaloItem {      // one ghost node: dst <- f(src, aux)
+    int dst, src, aux, mode;
+};
+
+enum : int { FLAG_NONFINITE = 1, FLAG_BAD_GRID = 2, FLAG_UNPHYSICAL = 4 };
+
+// HaloItem.mode: bits 0-3 kind, bits 4-5 direction, bit 6 side (1 = + face),
+// bits 8.. translation index (coordinates).
+enum : int { HM_COPY = 0, HM_WALL = 1, HM_FARFIELD = 2, HM_TRANSLATE = 3, HM_REFLECT = 4 };
+
+__host__ __device__ inline long long node_index(const DevBlock& B, int i, int j, int k) {
+    return B.base + i + (long long)j * B.sj + (long long)k * B.sk;
+}
+
+// ---------------------------------------------------------------------------
+// small math wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double hsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float hsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double hrcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float hrcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double habs(double x) { return fabs(x); }
+__device__ __forceinline__ float habs(float x) { return fabsf(x); }
+__device__ __forceinline__ double hmax0(double x) { return fmax(x, 0.0); }
+__device__ __forceinline__ float hmax0(float x) { return fmaxf(x, 0.0f); }
+__device__ __forceinline__ double hmin0(double x) { return fmin(x, 0.0); }
+__device__ __forceinline__ float hmin0(float x) { return fminf(x, 0.0f); }
+
+template <class R>
+struct GasR {   // gas constants in the working precision
+    R gamma, gm1, inv_2gamma, two_gm1, c3g, mach_re, kq_fac, suth, one_p_suth;
+    int mu_law;
+    __device__ __forceinline__ void init(const Gas& g) {
+        gamma = R(g.gamma);
+        gm1 = R(g.gamma - 1.0);
+        inv_2gamma = R(1.0 / (2.0 * g.gamma));
+        two_gm1 = R(2.0 * (g.gamma - 1.0));
+        c3g = R((3.0 - g.gamma) / (2.0 * (g.gamma - 1.0)));
+        mach_re = R(g.mach / g.re);
+        kq_fac = R(1.0 / (g.pr * (g.gamma - 1.0)));
+        suth = R(g.suth);
+        one_p_suth = R(1.0 + g.suth);
+        mu_law = g.mu_law;
+    }
+};
+
+// Sixth-order central first derivative (Sec. 2), unit spacing, from the six
+// neighbours fm3..fp3.
+template <class R>
+__device__ __forceinline__ R d6(R fm3, R fm2, R fm1, R fp1, R fp2, R fp3) {
+    return R(0.75) * (fp1 - fm1) + R(-0.15) * (fp2 - fm2) + R(1.0 / 60.0) * (fp3 - fm3);
+}
+
+// Face value at i+1/2 from nodes i-2..i+3 (sixth-order midpoint formula).
+template <class R>
+__device__ __forceinline__ R mid6(R fm2, R fm1, R f0, R fp1, R fp2, R fp3) {
+    return (R(3.0) * (fm2 + fp3) - R(25.0) * (fm1 + fp2) + R(150.0) * (f0 + fp1)) * R(1.0 / 256.0);
+}
+
+// Viscosity: mu = 1, or Sutherland T^(3/2) (1+S)/(T+S).
+template <class R>
+__device__ __forceinline__ R viscosity(const GasR<R>& g, R T) {
+    if (g.mu_law == 0) return R(1);
+    return T * hsqrt(T) * g.one_p_suth / (T + g.suth);
+}
+
+// ---------------------------------------------------------------------------
+// WENO5 interpolation of the modified AFWENO (Eqs. (13)-(17), Figs. 10-11):
+// from the 5-node stencil W[-2..2] of node i, the left-biased value at i+1/2
+// and the right-biased value at i-1/2, sharing the smoothness indicators.
+// Each sub-stencil is paired with its own indicator; linear weights 1/16,
+// 5/8, 5/16 for the stencils {i-2..i}, {i-1..i+1}, {i..i+2} (left value),
+// mirrored for the right value.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void weno_pair(double w0, double w1, double w2, double w3, double w4,
+                                          double& left, double& right) {
+    const double eps = 1.0e-6;
+    const double a1 = w0 - 2.0 * w1 + w2, c1 = w0 - 4.0 * w1 + 3.0 * w2;
+    const double a2 = w1 - 2.0 * w2 + w3, c2 = w1 - w3;
+    const double a3 = w2 - 2.0 * w3 + w4, c3 = 3.0 * w2 - 4.0 * w3 + w4;
+    const double b1 = (13.0 / 12.0) * a1 * a1 + 0.25 * c1 * c1;
+    const double b2 = (13.0 / 12.0) * a2 * a2 + 0.25 * c2 * c2;
+    const double b3 = (13.0 / 12.0) * a3 * a3 + 0.25 * c3 * c3;
+    double s1 = eps + b1, s2 = eps + b2, s3 = eps + b3;
+    s1 *= s1;
+    s2 *= s2;
+    s3 *= s3;
+    // gamma_j / s_j normalised == gamma_j * prod_{k != j} s_k normalised
+    const double p12 = s1 * s2, p13 = s1 * s3, p23 = s2 * s3;
+    const double uL1 = 0.375 * w0 - 1.25 * w1 + 1.875 * w2;
+    const double uL2 = -0.125 * w1 + 0.75 * w2 + 0.375 * w3;
+    const double uL3 = 0.375 * w2 + 0.75 * w3 - 0.125 * w4;
+    const double uR1 = 0.375 * w4 - 1.25 * w3 + 1.875 * w2;
+    const double uR2 = -0.125 * w3 + 0.75 * w2 + 0.375 * w1;
+    const double uR3 = 0.375 * w2 + 0.75 * w1 - 0.125 * w0;
+    const double tL1 = 0.0625 * p23, tL2 = 0.625 * p13, tL3 = 0.3125 * p12;
+    const double tR1 = 0.0625 * p12, tR2 = 0.625 * p13, tR3 = 0.3125 * p23;
+    left = (tL1 * uL1 + tL2 * uL2 + tL3 * uL3) / (tL1 + tL2 + tL3);
+    right = (tR1 * uR1 + tR2 * uR2 + tR3 * uR3) / (tR1 + tR2 + tR3);
+}
+
+__device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3, float w4, float& left,
+                                          float& right) {
+    const float eps = 1.0e-6f;
+    const float a1 = w0 - 2.0f * w1 + w2, c1 = w0 - 4.0f * w1 + 3.0f * w2;
+    const float a2 = w1 - 2.0f * w2 + w3, c2 = w1 - w3;
+    const float a3 = w2 - 2.0f * w3 + w4, c3 = 3.0f * w2 - 4.0f * w3 + w4;
+    const float b1 = (13.0f / 12.0f) * a1 * a1 + 0.25f * c1 * c1;
+    const float b2 = (13.0f / 12.0f) * a2 * a2 + 0.25f * c2 * c2;
+    const float b3 = (13.0f / 12.0f) * a3 * a3 + 0.25f * c3 * c3;
+    // reciprocal form: no overflow of products of squared indicators in FP32
+    float r1 = __frcp_rn(eps + b1), r2 = __frcp_rn(eps + b2), r3 = __frcp_rn(eps + b3);
+    r1 *= r1;
+    r2 *= r2;
+    r3 *= r3;
+    const float uL1 = 0.375f * w0 - 1.25f * w1 + 1.875f * w2;
+    const float uL2 = -0.125f * w1 + 0.75f * w2 + 0.375f * w3;
+    const float uL3 = 0.375f * w2 + 0.75f * w3 - 0.125f * w4;
+    const float uR1 = 0.375f * w4 - 1.25f * w3 + 1.875f * w2;
+    const float uR2 = -0.125f * w3 + 0.75f * w2 + 0.375f * w1;
+    const float uR3 = 0.375f * w2 + 0.75f * w1 - 0.125f * w0;
+    const float tL1 = 0.0625f * r1, tL2 = 0.625f * r2, tL3 = 0.3125f * r3;
+    const float tR1 = 0.0625f * r3, tR2 = 0.625f * r2, tR3 = 0.3125f * r1;
+    left = (tL1 * uL1 + tL2 * uL2 + tL3 * uL3) * __frcp_rn(tL1 + tL2 + tL3);
+    right = (tR1 * uR1 + tR2 * uR2 + tR3 * uR3) * __frcp_rn(tR1 + tR2 + tR3);
+}
+
+// ---------------------------------------------------------------------------
+// Characteristic basis at a node: Pulliam-Chaussee eigenvectors of the
+// Jacobian of k.F for the unit normal k of the node metric.  The projection
+// W = L Q and back projection U = R W are written in vector form:
+//   d = (Q_1 - u Q_0, Q_2 - v Q_0, Q_3 - w Q_0) / rho,
+//   S = (1 - phi2/c^2) Q_0 + (gamma-1)/c^2 (u Q_1 + v Q_2 + w Q_3 - Q_4),
+//   (W_0, W_1, W_2) = k S + d x k,
+//   W_3,4 = (c/rho (Q_0 - S) +- k.d) / sqrt(2),
+// and with C = k x (W_0, W_1, W_2), s = W_3 + W_4, t = W_3 - W_4, Wk = k.(W_0, W_1, W_2):
+//   U_0 = Wk + al s,  U_m = u_m Wk + rho C_m + al (s u_m + k_m c t)  (m = 1..3),
+//   U_4 = |u|^2/2 Wk + rho u.C + al (s H + c theta t),  al = rho/(sqrt(2) c),
+// which is the matrix pair L = T_k^-1, R = T_k entry by entry.
+// ---------------------------------------------------------------------------
+template <class R>
+struct CharBasis {
+    R kx, ky, kz, u, v, w, rho, irho, c, a0, g, cir, al, half_uu, H, cth;
+    __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
+        irho = hrcp(q[0]);
+        rho = q[0];
+        u = q[1] * irho;
+        v = q[2] * irho;
+        w = q[3] * irho;
+        half_uu = R(0.5) * (u * u + v * v + w * w);
+        const R p = gs.gm1 * (q[4] - rho * half_uu);
+        const R c2 = gs.gamma * p * irho;
+        c = hsqrt(c2);
+        const R ic = hrcp(c);
+        const R imm = hrcp(hsqrt(mx * mx + my * my + mz * mz));
+        kx = mx * imm;
+        ky = my * imm;
+        kz = mz * imm;
+        const R phi2 = gs.gm1 * half_uu;
+        const R ic2 = ic * ic;
+        a0 = R(1) - phi2 * ic2;
+        g = gs.gm1 * ic2;
+        cir = c * irho * R(0.70710678118654752440);
+        al = rho * ic * R(0.70710678118654752440);
+        H = half_uu + c2 / gs.gm1;
+        cth = c * (kx * u + ky * v + kz * w);
+    }
+    // W = L q
+    __device__ __forceinline__ void project(R q0, R q1, R q2, R q3, R q4, R W[5]) const {
+        const R d1 = (q1 - u * q0) * irho, d2 = (q2 - v * q0) * irho, d3 = (q3 - w * q0) * irho;
+        const R S = a0 * q0 + g * (u * q1 + v * q2 + w * q3 - q4);
+        W[0] = kx * S + (d2 * kz - d3 * ky);
+        W[1] = ky * S + (d3 * kx - d1 * kz);
+        W[2] = kz * S + (d1 * ky - d2 * kx);
+        const R kd = (kx * d1 + ky * d2 + kz * d3) * R(0.70710678118654752440);
+        const R base = cir * (q0 - S);
+        W[3] = base + kd;
+        W[4] = base - kd;
+    }
+    // U = R W
+    __device__ __forceinline__ void back(const R W[5], R U[5]) const {
+        const R Wk = kx * W[0] + ky * W[1] + kz * W[2];
+        const R Cx = ky * W[2] - kz * W[1], Cy = kz * W[0] - kx * W[2], Cz = kx * W[1] - ky * W[0];
+        const R s = W[3] + W[4], t = W[3] - W[4];
+        const R as = al * s, act = al * c * t;
+        U[0] = Wk + as;
+        U[1] = u * Wk + rho * Cx + as * u + act * kx;
+        U[2] = v * Wk + rho * Cy + as * v + act * ky;
+        U[3] = w * Wk + rho * Cz + as * w + act * kz;
+        U[4] = half_uu * Wk + rho * (u * Cx + v * Cy + w * Cz) + as * H + al * cth * t;
+    }
+};
+
+// Node flux along the conservative metric m, Eq. (4).
+template <class R>
+__device__ __forceinline__ void point_flux(const GasR<R>& gs, const R q[5], R mx, R my, R mz, R f[5]) {
+    const R irho = hrcp(q[0]);
+    const R u = q[1] * irho, v = q[2] * irho, w = q[3] * irho;
+    const R p = gs.gm1 * (q[4] - R(0.5) * (q[1] * u + q[2] * v + q[3] * w));
+    const R th = mx * u + my * v + mz * w;
+    f[0] = q[0] * th;
+    f[1] = q[1] * th + mx * p;
+    f[2] = q[2] * th + my * p;
+    f[3] = q[3] * th + mz * p;
+    f[4] = (q[4] + p) * th;
+}
+
+// Steger-Warming split flux along metric (kx, ky, kz) * mm; POS selects F+.
+//   F = rho/(2 gamma) [M, u M + c kx D, v M + c ky D, w M + c kz D,
+//                      (gamma-1) l1 |u|^2 + (l4+l5)(|u|^2+c^2)/2 + c theta D
+//                      + (l4+l5)(3-gamma) c^2 / (2 (gamma-1))]
+//   with l = lambda^+- of (theta, theta + c, theta - c) |m|, M = 2(gamma-1) l1 + l4 + l5, D = l4 - l5.
+template <class R, bool POS>
+__device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R kx, R ky, R kz, R mm, R F[5]) {
+    const R irho = hrcp(q[0]);
+    const R u = q[1] * irho, v = q[2] * irho, w = q[3] * irho;
+    const R uu = u * u + v * v + w * w;
+    const R p = gs.gm1 * (q[4] - R(0.5) * q[0] * uu);
+    const R c2 = gs.gamma * p * irho;
+    const R c = hsqrt(c2);
+    const R th = kx * u + ky * v + kz * w;
+    R l1 = th * mm, l4 = (th + c) * mm, l5 = (th - c) * mm;
+    if (POS) {
+        l1 = hmax0(l1);
+        l4 = hmax0(l4);
+        l5 = hmax0(l5);
+    } else {
+        l1 = hmin0(l1);
+        l4 = hmin0(l4);
+        l5 = hmin0(l5);
+    }
+    const R a = q[0] * gs.inv_2gamma;
+    const R S45 = l4 + l5, D45 = l4 - l5;
+    const R M = gs.two_gm1 * l1 + S45;
+    const R cD = c * D45;
+    F[0] = a * M;
+    F[1] = a * (u * M + kx * cD);
+    F[2] = a * (v * M + ky * cD);
+    F[3] = a * (w * M + kz * cD);
+    F[4] = a * (gs.gm1 * l1 * uu + R(0.5) * S45 * (uu + c2) + th * cD + S45 * c2 * gs.c3g);
+}
+
+// Viscous flux along metric m at a node, Eqs. (5)-(6): components 1..4
+// (the mass component is zero).  g = (u,v,w,T)_(x,y,z), row-major.
+template <class R>
+__device__ __forceinline__ void viscous_flux(const GasR<R>& gs, R u, R v, R w, R T, const R g[12], R mx, R my,
+                                             R mz, R fv[4]) {
+    const R kv = gs.mach_re * viscosity(gs, T);
+    const R kq = kv * gs.kq_fac;
+    const R div = g[0] + g[4] + g[8];
+    const R lam = R(-2.0 / 3.0) * kv * div;
+    const R txx = lam + R(2) * kv * g[0], tyy = lam + R(2) * kv * g[4], tzz = lam + R(2) * kv * g[8];
+    const R txy = kv * (g[1] + g[3]), txz = kv * (g[2] + g[6]), tyz = kv * (g[5] + g[7]);
+    const R bx = u * txx + v * txy + w * txz + kq * g[9];
+    const R by = u * txy + v * tyy + w * tyz + kq * g[10];
+    const R bz = u * txz + v * tyz + w * tzz + kq * g[11];
+    fv[0] = mx * txx + my * txy + mz * txz;
+    fv[1] = mx * txy + my * tyy + mz * tyz;
+    fv[2] = mx * txz + my * tyz + mz * tzz;
+    fv[3] = mx * bx + my * by + mz * bz;
+}
+
+// Derivative at node p of a line of n nodes from values f(-4..4) around it,
+// with the one-sided closure next to physical ends (boundary node
+// (-3,4,-1)/2, then 2nd-order central, then 4th-order central).
+template <class R, class F>
+__device__ __forceinline__ R dline(const F& f, int p, int n, bool lo, bool hi) {
+    if (lo && p <= 2) {
+        if (p == 0) return (R(-3) * f(0) + R(4) * f(1) - f(2)) * R(0.5);
+        if (p == 1) return (f(1) - f(-1)) * R(0.5);
+        return (f(-2) - R(8) * f(-1) + R(8) * f(1) - f(2)) * R(1.0 / 12.0);
+    }
+    if (hi && p >= n - 3) {
+        if (p == n - 1) return (R(3) * f(0) - R(4) * f(-1) + f(-2)) * R(0.5);
+        if (p == n - 2) return (f(1) - f(-1)) * R(0.5);
+        return (f(-2) - R(8) * f(-1) + R(8) * f(1) - f(2)) * R(1.0 / 12.0);
+    }
+    return d6<R>(f(-3), f(-2), f(-1), f(1), f(2), f(3));
+}
+
+}  // namespace hx

@@ -1,0 +1,48 @@
+// k_flux_dispatch.cu -- selects the flux instantiation for a precision,
+// direction, tile-shape variant and Euler / Navier-Stokes.
+#include "k_flux.cuh"
+#include "kernels.h"
+
+namespace hx {
+
+int flux_ctas_f64_d0(int, bool);
+int flux_ctas_f64_d1(int, bool);
+int flux_ctas_f64_d2(int, bool);
+int flux_ctas_f32_d0(int, bool);
+int flux_ctas_f32_d1(int, bool);
+int flux_ctas_f32_d2(int, bool);
+cudaError_t flux_run_f64_d0(int, bool, const FluxArgs&, cudaStream_t);
+cudaError_t flux_run_f64_d1(int, bool, const FluxArgs&, cudaStream_t);
+cudaError_t flux_run_f64_d2(int, bool, const FluxArgs&, cudaStream_t);
+cudaError_t flux_run_f32_d0(int, bool, const FluxArgs&, cudaStream_t);
+cudaError_t flux_run_f32_d1(int, bool, const FluxArgs&, cudaStream_t);
+cudaError_t flux_run_f32_d2(int, bool, const FluxArgs&, cudaStream_t);
+
+FluxShape flux_shape(int dir, int v) {
+    if (dir == 0) return v == 0 ? FluxShape{32, 8} : v == 1 ? FluxShape{16, 16} : FluxShape{64, 4};
+    return v == 0 ? FluxShape{8, 32} : v == 1 ? FluxShape{16, 16} : FluxShape{16, 32};
+}
+
+size_t flux_smem(bool fp64, int dir, int v, bool visc) {
+    const FluxShape sh = flux_shape(dir, v);
+    const int NP = sh.tp + 6, NU = sh.tp + 2;
+    const size_t SP = dir == 0 ? (size_t)sh.na * (NP + 1) : (size_t)NP * sh.na;
+    const size_t SU = dir == 0 ? (size_t)sh.na * (NU + 1) : (size_t)NU * sh.na;
+    return (fp64 ? 8 : 4) * (8 * SP + 10 * SU + (visc ? 4 * SP : 0));
+}
+
+int flux_ctas_per_sm(bool fp64, int dir, int v, bool visc) {
+    if (fp64) return dir == 0 ? flux_ctas_f64_d0(v, visc) : dir == 1 ? flux_ctas_f64_d1(v, visc) : flux_ctas_f64_d2(v, visc);
+    return dir == 0 ? flux_ctas_f32_d0(v, visc) : dir == 1 ? flux_ctas_f32_d1(v, visc) : flux_ctas_f32_d2(v, visc);
+}
+
+cudaError_t launch_flux(bool fp64, int dir, int v, bool visc, const FluxArgs& a, cudaStream_t s) {
+    if (a.ntiles <= 0) return cudaSuccess;
+    if (fp64)
+        return dir == 0 ? flux_run_f64_d0(v, visc, a, s) : dir == 1 ? flux_run_f64_d1(v, visc, a, s)
+                                                                  : flux_run_f64_d2(v, visc, a, s);
+    return dir == 0 ? flux_run_f32_d0(v, visc, a, s) : dir == 1 ? flux_run_f32_d1(v, visc, a, s)
+                                                              : flux_run_f32_d2(v, visc, a, s);
+}
+
+}  // namespace hx

@@ -1,0 +1,5 @@
+// Flux kernel instantiations: working precision double, direction 0.
+#define HX_FLUX_R double
+#define HX_FLUX_NAME f64_d
+#define HX_FLUX_DIR 0
+#include "k_flux_inst.cuh"

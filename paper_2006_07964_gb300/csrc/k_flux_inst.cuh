@@ -1,0 +1,72 @@
+// k_flux_inst.cuh -- instantiates the flux kernel for one working precision
+// (HX_FLUX_R) and one direction (HX_FLUX_DIR) in its own translation unit,
+// so the heavy instantiations compile in parallel.
+#include "k_flux.cuh"
+#include "kernels.h"
+
+#define HX_CAT3_(a, b, c) a##b##c
+#define HX_CAT3(a, b, c) HX_CAT3_(a, b, c)
+
+namespace hx {
+
+constexpr int flux_tp(int dir, int v) { return dir == 0 ? (v == 0 ? 32 : v == 1 ? 16 : 64) : (v == 0 ? 8 : 16); }
+constexpr int flux_na(int dir, int v) { return dir == 0 ? (v == 0 ? 8 : v == 1 ? 16 : 4) : (v == 0 ? 32 : v == 1 ? 16 : 32); }
+
+namespace {
+
+template <class R, int DIR, int V, bool VISC>
+struct FluxInst {
+    static constexpr int TP = flux_tp(DIR, V), NA = flux_na(DIR, V);
+    static constexpr size_t smem = FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC>();
+    static int ctas() {
+        auto kern = k_flux<R, DIR, TP, NA, VISC>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TP * NA, smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return nb;
+    }
+    static cudaError_t run(const FluxArgs& a, cudaStream_t s) {
+        k_flux<R, DIR, TP, NA, VISC><<<a.grid, TP * NA, smem, s>>>(
+            a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, a.fs, (const R*)a.prim, (const R*)a.grad,
+            (R*)a.A, a.accumulate, a.gas);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace
+
+int HX_CAT3(flux_ctas_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc) {
+    using R = HX_FLUX_R;
+    constexpr int D = HX_FLUX_DIR;
+    switch (v * 2 + (visc ? 1 : 0)) {
+        case 0: return FluxInst<R, D, 0, false>::ctas();
+        case 1: return FluxInst<R, D, 0, true>::ctas();
+        case 2: return FluxInst<R, D, 1, false>::ctas();
+        case 3: return FluxInst<R, D, 1, true>::ctas();
+        case 4: return FluxInst<R, D, 2, false>::ctas();
+        case 5: return FluxInst<R, D, 2, true>::ctas();
+    }
+    return 0;
+}
+
+cudaError_t HX_CAT3(flux_run_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc, const FluxArgs& a, cudaStream_t s) {
+    using R = HX_FLUX_R;
+    constexpr int D = HX_FLUX_DIR;
+    switch (v * 2 + (visc ? 1 : 0)) {
+        case 0: return FluxInst<R, D, 0, false>::run(a, s);
+        case 1: return FluxInst<R, D, 0, true>::run(a, s);
+        case 2: return FluxInst<R, D, 1, false>::run(a, s);
+        case 3: return FluxInst<R, D, 1, true>::run(a, s);
+        case 4: return FluxInst<R, D, 2, false>::run(a, s);
+        case 5: return FluxInst<R, D, 2, true>::run(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hx

@@ -1,0 +1,565 @@
+// k_misc.cu -- point-parallel kernels of the RK stage and of set-up:
+// layout packing, halo gathers, conservative metrics (Eqs. (7)-(8)),
+// primitives, chain-rule gradients (Eq. (21)), the RK3 combination
+// (Eq. (20)), physical-face node values and the CFL time step.
+#include "kernels.h"
+
+namespace hx {
+
+namespace {
+
+constexpr int kThreads = 256;   // brick kernels: 32 x 8 threads
+
+inline int grid_for(long long work, int per_cta = kThreads) {
+    long long g = (work + per_cta - 1) / per_cta;
+    if (g < 1) g = 1;
+    if (g > 152 * 64) g = 152 * 64;
+    return (int)g;
+}
+
+__device__ __forceinline__ void brick_node(const Brick& br, int& i, int& j, int& k, bool& ok) {
+    const int ti = threadIdx.x & 31, tj = threadIdx.x >> 5;
+    i = br.i0 + ti;
+    j = br.j0 + tj;
+    k = br.k0;
+    ok = ti < br.ni && tj < br.nj;
+}
+
+// ---------------------------------------------------------------- packing
+template <class T>
+__global__ void k_unpack(const double* __restrict__ src, T* __restrict__ dst, long long fs, DevBlock B, int nf) {
+    const long long N = (long long)B.n[0] * B.n[1] * B.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N * nf;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long f = t / N, r = t - f * N;
+        const int i = (int)(r % B.n[0]);
+        const long long r2 = r / B.n[0];
+        const int j = (int)(r2 % B.n[1]), k = (int)(r2 / B.n[1]);
+        dst[f * fs + node_index(B, i, j, k)] = (T)src[t];
+    }
+}
+
+__global__ void k_unpack2(const double* __restrict__ src, double* __restrict__ d64, float* __restrict__ d32,
+                          long long fs, DevBlock B, int nf) {
+    const long long N = (long long)B.n[0] * B.n[1] * B.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N * nf;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long f = t / N, r = t - f * N;
+        const int i = (int)(r % B.n[0]);
+        const long long r2 = r / B.n[0];
+        const int j = (int)(r2 % B.n[1]), k = (int)(r2 / B.n[1]);
+        const long long e = f * fs + node_index(B, i, j, k);
+        d64[e] = src[t];
+        if (d32) d32[e] = (float)src[t];
+    }
+}
+
+template <class T>
+__global__ void k_pack(const T* __restrict__ src, long long fs, DevBlock B, int nf, double* __restrict__ dst) {
+    const long long N = (long long)B.n[0] * B.n[1] * B.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N * nf;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long f = t / N, r = t - f * N;
+        const int i = (int)(r % B.n[0]);
+        const long long r2 = r / B.n[0];
+        const int j = (int)(r2 % B.n[1]), k = (int)(r2 / B.n[1]);
+        dst[t] = (double)src[f * fs + node_index(B, i, j, k)];
+    }
+}
+
+template <class T>
+__global__ void k_fill(T* p, long long n, T v) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        p[t] = v;
+}
+
+__global__ void k_cast(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        dst[t] = (float)src[t];
+}
+
+// ---------------------------------------------------------------- far field
+// State on a far-field node from the interior state qi (node next to the
+// boundary) and the outward unit normal n: 1D Riemann invariants along n,
+// outgoing R+ = u_n + 2c/(gamma-1) from the interior, incoming
+// R- = u_n - 2c/(gamma-1) from the free stream (rho = 1, u = (Ma, 0, 0),
+// p = 1/gamma, c = 1); entropy and tangential velocity from the upwind side.
+template <class R>
+__device__ void farfield_state(const GasR<R>& gs, R mach, const R qi[5], R nx, R ny, R nz, R qb[5]) {
+    const R g = gs.gamma, gm1 = gs.gm1;
+    const R irho = R(1) / qi[0];
+    const R u = qi[1] * irho, v = qi[2] * irho, w = qi[3] * irho;
+    const R p = gm1 * (qi[4] - R(0.5) * qi[0] * (u * u + v * v + w * w));
+    const R c = hsqrt(g * p * irho);
+    const R uni = nx * u + ny * v + nz * w;
+    const R unf = nx * mach;
+    R Rp = uni + R(2) * c / gm1;
+    R Rm = unf - R(2) / gm1;
+    if (unf <= R(-1)) Rp = unf + R(2) / gm1;
+    if (uni >= c) Rm = uni - R(2) * c / gm1;
+    const R un = R(0.5) * (Rp + Rm);
+    const R cb = R(0.25) * gm1 * (Rp - Rm);
+    R ent, tx, ty, tz;
+    if (un > R(0)) {
+        ent = p / pow(qi[0], g);
+        tx = u - uni * nx;
+        ty = v - uni * ny;
+        tz = w - uni * nz;
+    } else {
+        ent = (R(1) / g) / pow(R(1), g);
+        tx = mach - unf * nx;
+        ty = -unf * ny;
+        tz = -unf * nz;
+    }
+    const R rho = pow(cb * cb / (g * ent), R(1) / gm1);
+    const R pb = rho * cb * cb / g;
+    const R ub = tx + un * nx, vb = ty + un * ny, wb = tz + un * nz;
+    qb[0] = rho;
+    qb[1] = rho * ub;
+    qb[2] = rho * vb;
+    qb[3] = rho * wb;
+    qb[4] = pb / gm1 + R(0.5) * rho * (ub * ub + vb * vb + wb * wb);
+}
+
+// ---------------------------------------------------------------- halo
+// Ghost nodes of the state (face ghosts only): copy from the joined face's
+// node, wall mirror (rho, p even; velocity odd), or far-field state.
+template <class R>
+__global__ void k_halo(const HaloItem* __restrict__ items, int n, R* Q, long long fs, int nf,
+                       const R* __restrict__ met, Gas gas) {
+    GasR<R> gs;
+    gs.init(gas);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const HaloItem h = items[t];
+        const int kind = h.mode & 15;
+        if (kind == HM_COPY) {
+            for (int f = 0; f < nf; ++f) Q[f * fs + h.dst] = Q[f * fs + h.src];
+        } else if (kind == HM_WALL) {
+            Q[h.dst] = Q[h.src];
+            Q[fs + h.dst] = -Q[fs + h.src];
+            Q[2 * fs + h.dst] = -Q[2 * fs + h.src];
+            Q[3 * fs + h.dst] = -Q[3 * fs + h.src];
+            Q[4 * fs + h.dst] = Q[4 * fs + h.src];
+        } else if (kind == HM_FARFIELD) {
+            const int dir = (h.mode >> 4) & 3, side = (h.mode >> 6) & 1;
+            R m[3];
+            for (int c = 0; c < 3; ++c) m[c] = met[(3 * dir + c) * fs + h.aux];
+            const R sg = side ? R(1) : R(-1);
+            const R im = sg / hsqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            R qi[5], qb[5];
+            for (int c = 0; c < 5; ++c) qi[c] = Q[c * fs + h.src];
+            farfield_state(gs, R(gas.mach), qi, m[0] * im, m[1] * im, m[2] * im, qb);
+            for (int c = 0; c < 5; ++c) Q[c * fs + h.dst] = qb[c];
+        }
+    }
+}
+
+// Node values on physical faces after an RK stage: walls (u = 0,
+// e = p/(gamma-1)) in one launch, far fields (from the updated inward
+// node) in a second one.
+__global__ void k_bc_nodes(const HaloItem* __restrict__ items, int n, double* Q, float* Qf,
+                           const double* __restrict__ met, long long fs, Gas gas) {
+    GasR<double> gs;
+    gs.init(gas);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const HaloItem h = items[t];
+        const int kind = h.mode & 15;
+        double qb[5];
+        if (kind == HM_WALL) {
+            double q[5];
+            for (int c = 0; c < 5; ++c) q[c] = Q[c * fs + h.dst];
+            const double irho = 1.0 / q[0];
+            const double p = gs.gm1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * irho);
+            qb[0] = q[0];
+            qb[1] = qb[2] = qb[3] = 0.0;
+            qb[4] = p / gs.gm1;
+        } else {
+            const int dir = (h.mode >> 4) & 3, side = (h.mode >> 6) & 1;
+            double m[3], qi[5];
+            for (int c = 0; c < 3; ++c) m[c] = met[(3 * dir + c) * fs + h.aux];
+            const double im = (side ? 1.0 : -1.0) / sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            for (int c = 0; c < 5; ++c) qi[c] = Q[c * fs + h.src];
+            farfield_state(gs, gas.mach, qi, m[0] * im, m[1] * im, m[2] * im, qb);
+        }
+        for (int c = 0; c < 5; ++c) {
+            Q[c * fs + h.dst] = qb[c];
+            if (Qf) Qf[c * fs + h.dst] = (float)qb[c];
+        }
+    }
+}
+
+// Node coordinates: translated copy from the joined face, or point
+// reflection through the boundary node on physical faces.
+__global__ void k_halo_coords(const HaloItem* __restrict__ items, int n, double* X, long long fs,
+                              const double* __restrict__ tr) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const HaloItem h = items[t];
+        const int kind = h.mode & 15;
+        if (kind == HM_TRANSLATE) {
+            const int id = h.mode >> 8;
+            for (int c = 0; c < 3; ++c) X[c * fs + h.dst] = X[c * fs + h.src] + tr[3 * id + c];
+        } else {
+            for (int c = 0; c < 3; ++c) X[c * fs + h.dst] = 2.0 * X[c * fs + h.aux] - X[c * fs + h.src];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- metrics
+struct CoordView {
+    const double* X;
+    long long fs;
+    DevBlock B;
+    __device__ __forceinline__ double x(int c, int i, int j, int k) const {
+        return X[c * fs + node_index(B, i, j, k)];
+    }
+    // sixth-order derivative of coordinate c along axis a at (i, j, k)
+    __device__ __forceinline__ double dx(int c, int a, int i, int j, int k) const {
+        const long long st = a == 0 ? 1 : (a == 1 ? B.sj : B.sk);
+        const double* p = X + c * fs + node_index(B, i, j, k);
+        return d6<double>(p[-3 * st], p[-2 * st], p[-st], p[st], p[2 * st], p[3 * st]);
+    }
+    // outer derivative along ao of (d x_ci / d a_in) * x_cm
+    __device__ __forceinline__ double prod_d(int ci, int ain, int cm, int ao, int i, int j, int k) const {
+        double f[7];
+#pragma unroll
+        for (int s = -3; s <= 3; ++s) {
+            if (s == 0) continue;
+            const int ii = i + (ao == 0 ? s : 0), jj = j + (ao == 1 ? s : 0), kk = k + (ao == 2 ? s : 0);
+            f[s + 3] = dx(ci, ain, ii, jj, kk) * x(cm, ii, jj, kk);
+        }
+        return d6<double>(f[0], f[1], f[2], f[4], f[5], f[6]);
+    }
+};
+
+// Eq. (7): the nine conservative metrics, and Eq. (8): J^-1, on every node
+// of the bricks (interior and three ghost layers).
+__global__ void __launch_bounds__(kThreads)
+k_metrics(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ cblocks,
+          const double* __restrict__ X, long long fsc, const DevBlock* __restrict__ blocks, double* met,
+          long long fs, unsigned* flags) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const CoordView C{X, fsc, cblocks[br.b]};
+        enum { XI = 0, ETA = 1, ZETA = 2, CX = 0, CY = 1, CZ = 2 };
+        double m[10];
+        m[0] = C.prod_d(CY, ETA, CZ, ZETA, i, j, k) - C.prod_d(CY, ZETA, CZ, ETA, i, j, k);
+        m[1] = C.prod_d(CZ, ETA, CX, ZETA, i, j, k) - C.prod_d(CZ, ZETA, CX, ETA, i, j, k);
+        m[2] = C.prod_d(CX, ETA, CY, ZETA, i, j, k) - C.prod_d(CX, ZETA, CY, ETA, i, j, k);
+        m[3] = C.prod_d(CY, ZETA, CZ, XI, i, j, k) - C.prod_d(CY, XI, CZ, ZETA, i, j, k);
+        m[4] = C.prod_d(CZ, ZETA, CX, XI, i, j, k) - C.prod_d(CZ, XI, CX, ZETA, i, j, k);
+        m[5] = C.prod_d(CX, ZETA, CY, XI, i, j, k) - C.prod_d(CX, XI, CY, ZETA, i, j, k);
+        m[6] = C.prod_d(CY, XI, CZ, ETA, i, j, k) - C.prod_d(CY, ETA, CZ, XI, i, j, k);
+        m[7] = C.prod_d(CZ, XI, CX, ETA, i, j, k) - C.prod_d(CZ, ETA, CX, XI, i, j, k);
+        m[8] = C.prod_d(CX, XI, CY, ETA, i, j, k) - C.prod_d(CX, ETA, CY, XI, i, j, k);
+        const double xx = C.dx(CX, XI, i, j, k), xe = C.dx(CX, ETA, i, j, k), xz = C.dx(CX, ZETA, i, j, k);
+        const double yx = C.dx(CY, XI, i, j, k), ye = C.dx(CY, ETA, i, j, k), yz = C.dx(CY, ZETA, i, j, k);
+        const double zx = C.dx(CZ, XI, i, j, k), ze = C.dx(CZ, ETA, i, j, k), zz = C.dx(CZ, ZETA, i, j, k);
+        const double jinv =
+            xx * ye * zz - xx * yz * ze + xe * yz * zx - xe * yx * zz + xz * yx * ze - xz * ye * zx;
+        if (!(jinv > 0.0)) atomicOr(flags, (unsigned)FLAG_BAD_GRID);
+        m[9] = 1.0 / jinv;
+        const long long e = node_index(blocks[br.b], i, j, k);
+        for (int c = 0; c < 10; ++c) met[c * fs + e] = m[c];
+    }
+}
+
+// ---------------------------------------------------------------- primitives
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+k_prim(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const R* __restrict__ Q,
+       long long fs, R* __restrict__ prim, Gas gas) {
+    GasR<R> gs;
+    gs.init(gas);
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const long long e = node_index(blocks[br.b], i, j, k);
+        const R q0 = Q[e], q1 = Q[fs + e], q2 = Q[2 * fs + e], q3 = Q[3 * fs + e], q4 = Q[4 * fs + e];
+        const R irho = hrcp(q0);
+        const R u = q1 * irho, v = q2 * irho, w = q3 * irho;
+        const R p = gs.gm1 * (q4 - R(0.5) * (q1 * u + q2 * v + q3 * w));
+        prim[e] = u;
+        prim[fs + e] = v;
+        prim[2 * fs + e] = w;
+        prim[3 * fs + e] = gs.gamma * p * irho;
+    }
+}
+
+// Eq. (21): (u, v, w, T)_(x, y, z) = J * sum_d m^_d (.)_(xi_d), derivatives
+// by the sixth-order operator or the physical-face closure.
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const R* __restrict__ prim,
+       const R* __restrict__ met, long long fs, R* __restrict__ grad) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const DevBlock B = blocks[br.b];
+        const long long e = node_index(B, i, j, k);
+        const int id[3] = {i, j, k};
+        R dc[4][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const long long st = a == 0 ? 1 : (a == 1 ? B.sj : B.sk);
+            const bool lo = (B.phys >> (2 * a)) & 1, hi = (B.phys >> (2 * a + 1)) & 1;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const R* f0 = prim + v * fs + e;
+                auto f = [&](int s) { return f0[s * st]; };
+                dc[v][a] = dline<R>(f, id[a], B.n[a], lo, hi);
+            }
+        }
+        const R J = met[9 * fs + e];
+        R m[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) m[c] = met[c * fs + e];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                grad[(v * 3 + c) * fs + e] = J * (m[c] * dc[v][0] + m[3 + c] * dc[v][1] + m[6 + c] * dc[v][2]);
+    }
+}
+
+// ---------------------------------------------------------------- RK3 stage
+// Eq. (20) in FP64: Q_out = ca Q^n + cb Q^(k) + cc dt R, R = -J A (Eqs.
+// (2)-(3)); wall nodes then get u = 0, e = p/(gamma-1); the mixed form also
+// writes the FP32 copy the stencil kernels read.
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+k_rk(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const double* Qn,
+     const double* Qk, const R* __restrict__ A, const double* __restrict__ met, long long fs, double* Qout,
+     float* Qf, double ca, double cb, double cc, double gm1, unsigned* flags) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const DevBlock B = blocks[br.b];
+        const long long e = node_index(B, i, j, k);
+        const double f = -cc * B.dt * met[9 * fs + e];
+        double q[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const double a = (double)A[c * fs + e];
+            double v = ca * Qn[c * fs + e] + f * a;
+            if (cb != 0.0) v += cb * Qk[c * fs + e];
+            q[c] = v;
+        }
+        if (B.wall) {
+            const bool on = ((B.wall & 1) && i == 0) || ((B.wall & 2) && i == B.n[0] - 1) ||
+                            ((B.wall & 4) && j == 0) || ((B.wall & 8) && j == B.n[1] - 1) ||
+                            ((B.wall & 16) && k == 0) || ((B.wall & 32) && k == B.n[2] - 1);
+            if (on) {
+                const double p = gm1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+                q[1] = q[2] = q[3] = 0.0;
+                q[4] = p / gm1;
+            }
+        }
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            finite = finite && isfinite(q[c]);
+            Qout[c * fs + e] = q[c];
+            if (Qf) Qf[c * fs + e] = (float)q[c];
+        }
+        if (!finite) atomicOr(flags, (unsigned)FLAG_NONFINITE);
+        else if (!(q[0] > 0.0) || !(q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0] > 0.0))
+            atomicOr(flags, (unsigned)FLAG_UNPHYSICAL);
+    }
+}
+
+// Residual R = -J A of one block, packed [5][nk][nj][ni].
+template <class R>
+__global__ void k_rhs_out(DevBlock B, const R* __restrict__ A, const double* __restrict__ met, long long fs,
+                          double* __restrict__ out) {
+    const long long N = (long long)B.n[0] * B.n[1] * B.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N * 5;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long f = t / N, r = t - f * N;
+        const int i = (int)(r % B.n[0]);
+        const long long r2 = r / B.n[0];
+        const int j = (int)(r2 % B.n[1]), k = (int)(r2 / B.n[1]);
+        const long long e = node_index(B, i, j, k);
+        out[t] = -met[9 * fs + e] * (double)A[f * fs + e];
+    }
+}
+
+// ---------------------------------------------------------------- CFL
+// Per block: max over nodes of sum_d (|m_d . u| + c |m_d|) J, as the bits of
+// a non-negative double (monotone under unsigned comparison).
+__global__ void __launch_bounds__(kThreads)
+k_dt(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const double* __restrict__ Q,
+     const double* __restrict__ met, long long fs, Gas gas, unsigned long long* bmax) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        double s = 0.0;
+        if (ok) {
+            const DevBlock B = blocks[br.b];
+            const long long e = node_index(B, i, j, k);
+            const double irho = 1.0 / Q[e];
+            const double u = Q[fs + e] * irho, v = Q[2 * fs + e] * irho, w = Q[3 * fs + e] * irho;
+            const double p = (gas.gamma - 1.0) * (Q[4 * fs + e] - 0.5 * Q[e] * (u * u + v * v + w * w));
+            const double c = sqrt(gas.gamma * p * irho);
+            const double J = met[9 * fs + e];
+            for (int d = 0; d < 3; ++d) {
+                const double mx = met[(3 * d) * fs + e], my = met[(3 * d + 1) * fs + e],
+                             mz = met[(3 * d + 2) * fs + e];
+                s += (fabs(mx * u + my * v + mz * w) + c * sqrt(mx * mx + my * my + mz * mz)) * J;
+            }
+        }
+        unsigned long long bits = __double_as_longlong(s);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+            bits = other > bits ? other : bits;
+        }
+        if ((threadIdx.x & 31) == 0) atomicMax(&bmax[br.b], bits);
+    }
+}
+
+}  // namespace
+
+// ====================================================================== launchers
+
+cudaError_t launch_unpack(const double* src, void* dst, bool fp64, long long fs, DevBlock B, int nf,
+                          cudaStream_t s) {
+    const long long n = (long long)B.n[0] * B.n[1] * B.n[2] * nf;
+    if (fp64)
+        k_unpack<double><<<grid_for(n), kThreads, 0, s>>>(src, (double*)dst, fs, B, nf);
+    else
+        k_unpack<float><<<grid_for(n), kThreads, 0, s>>>(src, (float*)dst, fs, B, nf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack2(const double* src, double* d64, float* d32, long long fs, DevBlock B, int nf,
+                           cudaStream_t s) {
+    const long long n = (long long)B.n[0] * B.n[1] * B.n[2] * nf;
+    k_unpack2<<<grid_for(n), kThreads, 0, s>>>(src, d64, d32, fs, B, nf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const void* src, bool fp64, long long fs, DevBlock B, int nf, double* dst,
+                        cudaStream_t s) {
+    const long long n = (long long)B.n[0] * B.n[1] * B.n[2] * nf;
+    if (fp64)
+        k_pack<double><<<grid_for(n), kThreads, 0, s>>>((const double*)src, fs, B, nf, dst);
+    else
+        k_pack<float><<<grid_for(n), kThreads, 0, s>>>((const float*)src, fs, B, nf, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(void* p, bool fp64, long long n, double v, cudaStream_t s) {
+    if (fp64)
+        k_fill<double><<<grid_for(n), kThreads, 0, s>>>((double*)p, n, v);
+    else
+        k_fill<float><<<grid_for(n), kThreads, 0, s>>>((float*)p, n, (float)v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast(const double* src, float* dst, long long n, cudaStream_t s) {
+    k_cast<<<grid_for(n), kThreads, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo(const HaloItem* items, int n, void* Q, bool fp64, long long fs, int nf, const void* met,
+                        Gas gas, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (fp64)
+        k_halo<double><<<grid_for(n), kThreads, 0, s>>>(items, n, (double*)Q, fs, nf, (const double*)met, gas);
+    else
+        k_halo<float><<<grid_for(n), kThreads, 0, s>>>(items, n, (float*)Q, fs, nf, (const float*)met, gas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_coords(const HaloItem* items, int n, double* X, long long fs, const double* tr,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_halo_coords<<<grid_for(n), kThreads, 0, s>>>(items, n, X, fs, tr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bc_nodes(const HaloItem* items, int n, double* Q, float* Qf, const double* met, long long fs,
+                            Gas gas, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_bc_nodes<<<grid_for(n), kThreads, 0, s>>>(items, n, Q, Qf, met, fs, gas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_metrics(const Brick* bricks, int nb, const DevBlock* cblocks, const double* X, long long fsc,
+                           const DevBlock* blocks, double* met, long long fs, unsigned* flags, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    k_metrics<<<grid_for((long long)nb * kThreads), kThreads, 0, s>>>(bricks, nb, cblocks, X, fsc, blocks, met, fs,
+                                                                      flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, const void* Q, bool fp64,
+                        long long fs, void* prim, Gas gas, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    const int g = grid_for((long long)nb * kThreads);
+    if (fp64)
+        k_prim<double><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const double*)Q, fs, (double*)prim, gas);
+    else
+        k_prim<float><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)Q, fs, (float*)prim, gas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, const void* prim, const void* met,
+                        bool fp64, long long fs, void* grad, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    const int g = grid_for((long long)nb * kThreads);
+    if (fp64)
+        k_grad<double><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const double*)prim, (const double*)met, fs,
+                                              (double*)grad);
+    else
+        k_grad<float><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)prim, (const float*)met, fs,
+                                             (float*)grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk(const Brick* bricks, int nb, const DevBlock* blocks, const double* Qn, const double* Qk,
+                      const void* A, bool fp64, const double* met, long long fs, double* Qout, float* Qf,
+                      double ca, double cb, double cc, double gm1, unsigned* flags, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    const int g = grid_for((long long)nb * kThreads);
+    if (fp64)
+        k_rk<double><<<g, kThreads, 0, s>>>(bricks, nb, blocks, Qn, Qk, (const double*)A, met, fs, Qout, Qf, ca, cb,
+                                            cc, gm1, flags);
+    else
+        k_rk<float><<<g, kThreads, 0, s>>>(bricks, nb, blocks, Qn, Qk, (const float*)A, met, fs, Qout, Qf, ca, cb,
+                                           cc, gm1, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt(const Brick* bricks, int nb, const DevBlock* blocks, const double* Q, const double* met,
+                      long long fs, Gas gas, unsigned long long* bmax, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    k_dt<<<grid_for((long long)nb * kThreads), kThreads, 0, s>>>(bricks, nb, blocks, Q, met, fs, gas, bmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_out(DevBlock B, const void* A, bool fp64, const double* met, long long fs, double* out,
+                           cudaStream_t s) {
+    const long long n = (long long)B.n[0] * B.n[1] * B.n[2] * 5;
+    if (fp64)
+        k_rhs_out<double><<<grid_for(n), kThreads, 0, s>>>(B, (const double*)A, met, fs, out);
+    else
+        k_rhs_out<float><<<grid_for(n), kThreads, 0, s>>>(B, (const float*)A, met, fs, out);
+    return cudaGetLastError();
+}
+
+}  // namespace hx

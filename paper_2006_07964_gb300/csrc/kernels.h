@@ -1,0 +1,68 @@
+// kernels.h -- host-side launchers of the device kernels (one per kernel
+// family); the runtime calls only these.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hx_common.cuh"
+
+namespace hx {
+
+// ---- fused per-direction flux kernel (k_flux.cuh) ------------------------
+struct FluxArgs {
+    const DevBlock* blocks;
+    const Tile* tiles;
+    int ntiles;
+    const void* Q;      // R, 5 fields
+    const void* met;    // R, 10 fields
+    long long fs;       // field stride (elements)
+    const void* prim;   // R, 4 fields (u, v, w, T), Navier-Stokes only
+    const void* grad;   // R, 12 fields, Navier-Stokes only
+    void* A;            // R, 5 fields, accumulated divergence
+    int accumulate;
+    Gas gas;
+    int grid;           // CTAs of the persistent launch
+};
+
+struct FluxShape {
+    int tp, na;         // nodes along the sweep, lines across
+};
+
+constexpr int kFluxVariants = 3;
+FluxShape flux_shape(int dir, int variant);
+size_t flux_smem(bool fp64, int dir, int variant, bool visc);
+// CTAs per SM the variant can keep resident (0 if it cannot launch).
+int flux_ctas_per_sm(bool fp64, int dir, int variant, bool visc);
+cudaError_t launch_flux(bool fp64, int dir, int variant, bool visc, const FluxArgs& a, cudaStream_t s);
+
+// ---- everything else (k_misc.cu) ----------------------------------------
+// Unpack a host-layout array [nf][nk][nj][ni] (double) into the padded layout.
+cudaError_t launch_unpack(const double* src, void* dst, bool dst_fp64, long long fs, DevBlock B, int nf,
+                          cudaStream_t s);
+// Same for a second, FP32 copy (nullable).
+cudaError_t launch_unpack2(const double* src, double* dst64, float* dst32, long long fs, DevBlock B, int nf,
+                           cudaStream_t s);
+cudaError_t launch_pack(const void* src, bool src_fp64, long long fs, DevBlock B, int nf, double* dst,
+                        cudaStream_t s);
+cudaError_t launch_halo(const HaloItem* items, int n, void* Q, bool fp64, long long fs, int nfields,
+                        const void* met, Gas gas, cudaStream_t s);
+cudaError_t launch_halo_coords(const HaloItem* items, int n, double* X, long long fs, const double* tr,
+                               cudaStream_t s);
+cudaError_t launch_metrics(const Brick* bricks, int nb, const DevBlock* cblocks, const double* X, long long fsc,
+                           const DevBlock* blocks, double* met, long long fs, unsigned* flags, cudaStream_t s);
+cudaError_t launch_cast(const double* src, float* dst, long long n, cudaStream_t s);
+cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, const void* Q, bool fp64,
+                        long long fs, void* prim, Gas gas, cudaStream_t s);
+cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, const void* prim, const void* met,
+                        bool fp64, long long fs, void* grad, cudaStream_t s);
+cudaError_t launch_rk(const Brick* bricks, int nb, const DevBlock* blocks, const double* Qn, const double* Qk,
+                      const void* A, bool fp64, const double* met, long long fs, double* Qout, float* Qf,
+                      double ca, double cb, double cc, double gm1, unsigned* flags, cudaStream_t s);
+cudaError_t launch_bc_nodes(const HaloItem* items, int n, double* Q, float* Qf, const double* met, long long fs,
+                            Gas gas, cudaStream_t s);
+cudaError_t launch_dt(const Brick* bricks, int nb, const DevBlock* blocks, const double* Q, const double* met,
+                      long long fs, Gas gas, unsigned long long* bmax, cudaStream_t s);
+cudaError_t launch_rhs_out(DevBlock B, const void* A, bool fp64, const double* met, long long fs, double* out,
+                           cudaStream_t s);
+cudaError_t launch_fill(void* p, bool fp64, long long n, double v, cudaStream_t s);
+
+}  // namespace hx

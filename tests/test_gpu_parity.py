@@ -1,0 +1,320 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
+element by element on the same seeded inputs.
+
+Tolerance (FP64 form): relative L-infinity per variable group (the components
+of a vector share its scale; the residual uses one scale for all five),
+max|gpu - oracle| / max|oracle| <= 1e-11, after the stated steps.  The
+residual R is compared against its largest component.  Sizes span
+several tiles with ragged tails; full sizes of the benchmark workloads are
+compared on whole fields (the oracle is fast enough), plus multi-block,
+physical faces, per-block time steps and the error paths of the ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_07964_gb300 import build, hx
+from paper_2006_07964_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    build.build()
+    hx.load()
+    oracle.set_threads(max(1, oracle.max_threads()))
+
+
+# Components of one vector share a scale: a component that is zero in exact
+# arithmetic (w on an extruded grid, the z parts of xi^, eta^) holds only
+# rounding noise and is measured against its vector's magnitude.
+GROUPS = {
+    "state": [[0], [1, 2, 3], [4]],
+    "rhs": [[0, 1, 2, 3, 4]],
+    "met": [[0, 1, 2], [3, 4, 5], [6, 7, 8], [9]],
+    "grad": [list(range(12))],
+}
+
+
+def rel_linf(a, b, kind="state"):
+    """max over groups of max|a - b| / max|b| (relative L-infinity)."""
+    a, b = np.asarray(a), np.asarray(b)
+    out = []
+    for g in GROUPS[kind]:
+        s = np.abs(b[g]).max()
+        out.append(np.abs(a[g] - b[g]).max() / (s if s > 0 else 1.0))
+    return max(out)
+
+
+def warped(dims, amp=0.08, L=10.0, viscous=False, reynolds=200.0, mu_law=1, free_stream=False):
+    ni, nj, nk = dims
+    Ls = (L, L * nj / ni, L * nk / ni)
+    xyz = W.warped_box((ni, nj, nk), Ls, amp)
+    g = 1.4
+    if free_stream:
+        q = W.conservative(g, np.ones(xyz.shape[1:]), 0.5, 0.2, 0.1, 1.0 / g)
+    else:
+        q = W.conservative(g, *W.isentropic_vortex(g, xyz[0], xyz[1], L=L, centre=(0.5 * L, 0.5 * Ls[1])))
+    return W.Workload("warped%dx%dx%d" % dims, [W.Block(xyz, W.periodic_faces(Ls), q)], gamma=g, mach=0.5,
+                      reynolds=reynolds, viscous=viscous, mu_law=mu_law, meta={"L": Ls})
+
+
+def split(w, parts):
+    blocks = W.split_periodic_box(w.blocks[0].xyz, w.meta["L"], parts)
+    for b, q in zip(blocks, W.split_state(w.blocks[0].q0, parts)):
+        b.q0 = q
+    return W.Workload(w.name + "_split", blocks, gamma=w.gamma, mach=w.mach, reynolds=w.reynolds,
+                      prandtl=w.prandtl, viscous=w.viscous, mu_law=w.mu_law)
+
+
+CASES = {
+    "vortex32": lambda: W.vortex(32),
+    "ragged_euler": lambda: warped((37, 29, 23)),
+    "ragged_ns": lambda: warped((33, 26, 19), viscous=True),
+    "tgv24": lambda: W.tgv(24),
+    "split_ns": lambda: split(warped((30, 24, 20), viscous=True, reynolds=100.0), (2, 2, 1)),
+    "ogrid_s4": lambda: W.ogrid(scale=4),
+    "ogrid_s8": lambda: W.ogrid(scale=8),
+}
+
+
+def pair(name, precision="fp64"):
+    w = CASES[name]()
+    return w, hx.from_workload(w, precision=precision), oracle.from_workload(w)
+
+
+# ---------------------------------------------------------------- metrics, dt
+
+@pytest.mark.parametrize("name", ["vortex32", "ragged_euler", "split_ns", "ogrid_s4"])
+def test_metrics_parity(name):
+    w, ctx, P = pair(name)
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.get_metrics(b), P.get_metrics(b), "met") < 1e-13
+
+
+@pytest.mark.parametrize("name", ["vortex32", "tgv24", "ogrid_s4"])
+def test_dt_parity(name):
+    w, ctx, P = pair(name)
+    g1, per1 = ctx.compute_dt(0.5)
+    g2, per2 = P.dt(0.5)
+    assert g1 == pytest.approx(g2, rel=1e-13)
+    assert np.allclose(per1, per2, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- residual
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_parity(name):
+    w, ctx, P = pair(name)
+    P.rhs()
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.rhs(b), P.get_rhs(b), "rhs") < TOL, (name, b)
+
+
+@pytest.mark.parametrize("name", ["ragged_ns", "tgv24", "split_ns", "ogrid_s8"])
+def test_gradient_parity(name):
+    w, ctx, P = pair(name)
+    P.rhs()
+    for b in range(len(w.blocks)):
+        ctx.rhs(b)
+        assert rel_linf(ctx.get_gradients(b), P.get_grad(b), "grad") < TOL, (name, b)
+
+
+def test_free_stream_residual_gpu():
+    w = W.vortex(32, free_stream=True)
+    ctx = hx.from_workload(w)
+    assert np.abs(ctx.rhs(0)).max() < 1e-12
+
+
+# ---------------------------------------------------------------- steps
+
+@pytest.mark.parametrize("name,steps", [("vortex32", 10), ("ragged_euler", 4), ("tgv24", 5), ("split_ns", 3),
+                                        ("ogrid_s4", 5)])
+def test_steps_parity(name, steps):
+    w, ctx, P = pair(name)
+    dt, _ = P.dt(0.5)
+    ctx.step(steps, dt)
+    P.step(steps, dt)
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.get_state(b), P.get_state(b)) < TOL, (name, b)
+
+
+def test_batch_per_block_dt_parity():
+    w = W.batch(count=5, seed=7, steps=3)
+    ctx = hx.from_workload(w)
+    P = oracle.from_workload(w)
+    _, per = P.dt(0.5)
+    _, per_gpu = ctx.compute_dt(0.5)
+    assert np.allclose(per, per_gpu, rtol=1e-13)
+    ctx.step(3, per)
+    P.step(3, per)
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.get_state(b), P.get_state(b)) < TOL
+
+
+@pytest.mark.slow
+def test_full_size_tgv128_two_steps():
+    """The Taylor-Green workload at its full 128^3 size, two RK3 steps, every node."""
+    w = W.tgv(128)
+    ctx = hx.from_workload(w)
+    P = oracle.from_workload(w)
+    dt, _ = P.dt(0.5)
+    ctx.step(2, dt)
+    P.step(2, dt)
+    assert rel_linf(ctx.get_state(0), P.get_state(0)) < TOL
+
+
+@pytest.mark.slow
+def test_full_size_ogrid_residual_and_step():
+    """The 8-block O-grid at full size (3,538,944 nodes): residual of every
+    block, then one RK3 step."""
+    w = W.ogrid()
+    ctx = hx.from_workload(w)
+    P = oracle.from_workload(w)
+    P.rhs()
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.rhs(b), P.get_rhs(b), "rhs") < TOL, b
+    dt, _ = P.dt(0.5)
+    ctx.step(1, dt)
+    P.step(1, dt)
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.get_state(b), P.get_state(b)) < TOL, b
+
+
+# ---------------------------------------------------------------- invariants on the GPU
+
+def test_conservation_gpu():
+    w = W.tgv(20)
+    ctx = hx.from_workload(w)
+    J = ctx.get_metrics(0)[9]
+    tot0 = (w.blocks[0].q0 / J).sum(axis=(1, 2, 3))
+    dt, _ = ctx.compute_dt(0.5)
+    ctx.step(5, dt)
+    tot = (ctx.get_state(0) / J).sum(axis=(1, 2, 3))
+    scale = np.abs(w.blocks[0].q0 / J).sum(axis=(1, 2, 3)).max()
+    assert np.abs(tot - tot0).max() < 1e-13 * scale
+
+
+def test_graph_replay_equals_profiled_launches():
+    w = W.tgv(16)
+    a = hx.from_workload(w)
+    b = hx.from_workload(w)
+    dt, _ = a.compute_dt(0.5)
+    a.step(3, dt)
+    stats = b.profile_step(3, dt)
+    assert np.array_equal(a.get_state(0), b.get_state(0))
+    assert stats["flux_xi"][0] == 9 and stats["rk_update"][0] == 9
+
+
+def test_checkpoint_resume_bitwise():
+    w = W.tgv(16)
+    a = hx.from_workload(w)
+    dt, _ = a.compute_dt(0.5)
+    a.step(4, dt)
+    ref = a.get_state(0)
+    b = hx.from_workload(w)
+    b.step(2, dt)
+    mid = b.get_state(0)
+    b.close()
+    c = hx.from_workload(w)
+    c.set_state(0, mid)
+    c.step(2, dt)
+    assert np.array_equal(c.get_state(0), ref)
+
+
+def test_device_pointer_state_roundtrip():
+    torch = pytest.importorskip("torch")
+    w = W.vortex(16)
+    ctx = hx.from_workload(w)
+    q = torch.tensor(w.blocks[0].q0, dtype=torch.float64, device="cuda")
+    ctx.set_state(0, q * 1.0)
+    out = torch.empty_like(q)
+    ctx.get_state(0, out)
+    assert torch.equal(out, q)
+
+
+# ---------------------------------------------------------------- mixed precision
+
+def test_mixed_precision_error_vs_oracle():
+    """FP32 state, fluxes and WENO, FP64 metrics and RK combination: relative
+    L2 error of rho, rho u, E after 10 steps of the 32^3 vortex <= 1e-5."""
+    w = W.vortex(32)
+    ctx = hx.from_workload(w, precision="mixed")
+    P = oracle.from_workload(w)
+    dt, _ = P.dt(0.5)
+    ctx.step(10, dt)
+    P.step(10, dt)
+    a, b = ctx.get_state(0), P.get_state(0)
+    for v in (0, 1, 4):
+        rel_l2 = np.linalg.norm(a[v] - b[v]) / np.linalg.norm(b[v])
+        assert rel_l2 < 1e-5, (v, rel_l2)
+
+
+def test_mixed_precision_rhs_close():
+    w = W.tgv(24)
+    ctx = hx.from_workload(w, precision="mixed")
+    P = oracle.from_workload(w)
+    P.rhs()
+    assert rel_linf(ctx.rhs(0), P.get_rhs(0), "rhs") < 1e-4
+
+
+# ---------------------------------------------------------------- error paths
+
+def test_error_topology():
+    w = W.vortex(8)
+    ctx = hx.Context()
+    ctx.add_block(w.blocks[0].xyz)
+    for f in range(6):
+        ctx.set_face(0, f, "periodic", 0, f)   # not the opposite face
+    with pytest.raises(hx.HxError) as ei:
+        ctx.finalize()
+    assert ei.value.name == "HX_ERR_TOPOLOGY"
+
+
+def test_error_bad_grid():
+    w = W.vortex(8)
+    xyz = w.blocks[0].xyz.copy()
+    xyz[0] = -xyz[0]        # mirrored grid: J^-1 < 0
+    ctx = hx.Context()
+    ctx.add_block(xyz)
+    for f, face in enumerate(W.periodic_faces((-10.0, 10.0, 10.0))):
+        ctx.set_face(0, f, face.kind, face.nbr, face.nbr_face, face.translate)
+    ctx.finalize()
+    with pytest.raises(hx.HxError) as ei:
+        ctx.compute_metrics()
+    assert ei.value.name == "HX_ERR_BAD_GRID"
+
+
+def test_error_nonfinite_and_state_order():
+    w = W.vortex(12)
+    ctx = hx.Context()
+    ctx.add_block(w.blocks[0].xyz)
+    for f, face in enumerate(w.blocks[0].faces):
+        ctx.set_face(0, f, face.kind, face.nbr, face.nbr_face, face.translate)
+    ctx.finalize()
+    with pytest.raises(hx.HxError) as ei:
+        ctx.step(1, 0.01)
+    assert ei.value.name == "HX_ERR_STATE"
+    ctx.compute_metrics()
+    q = w.blocks[0].q0.copy()
+    q[0, 3, 4, 5] = np.nan
+    ctx.set_state(0, q)
+    with pytest.raises(hx.HxError) as ei:
+        ctx.step(1, 0.01)
+    assert ei.value.name == "HX_ERR_NONFINITE"
+
+
+def test_error_memory_cap():
+    w = W.vortex(16)
+    with pytest.raises(hx.HxError) as ei:
+        hx.from_workload(w, mem_cap_bytes=1 << 20)
+    assert ei.value.name == "HX_ERR_OOM"
+
+
+def test_error_invalid_args():
+    ctx = hx.Context()
+    with pytest.raises(hx.HxError):
+        ctx.add_block(np.zeros((3, 4, 4, 4)))
+    with pytest.raises(hx.HxError):
+        ctx.finalize()
