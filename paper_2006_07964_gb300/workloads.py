@@ -283,8 +283,10 @@ def ogrid(scale=1, steps=100, mach=0.2, reynolds=3900.0, prandtl=0.71, sectors=(
     i runs around the cylinder (clockwise, so that J > 0) through four sectors
     of uneven width; j runs outward through an inner and an outer layer
     (geometric stretching, first cell 1e-3 at full size); k is spanwise over
-    L_z = pi, periodic.  Block (s, l) = sector s, layer l.  scale > 1 divides
-    every count by `scale` for reduced-size tests."""
+    L_z = pi, periodic.  Block (s, l) = sector s, layer l.  The initial state
+    is the potential flow past the cylinder at free-stream Mach `mach` with
+    the wall nodes at rest.  scale > 1 divides every count by `scale` for
+    reduced-size tests."""
     sec = [max(6, s // scale) for s in sectors]
     lay = [max(6, l // scale) for l in layers]
     nz = max(6, nz // scale)
@@ -313,11 +315,20 @@ def ogrid(scale=1, steps=100, mach=0.2, reynolds=3900.0, prandtl=0.71, sectors=(
                 Face("periodic", bid, 5, (0.0, 0.0, -Lz)),
                 Face("periodic", bid, 4, (0.0, 0.0, Lz)),
             ]
-            rho = np.ones(xyz.shape[1:])
-            u = np.full(rho.shape, mach)
+            # potential flow past the cylinder (radius a = 0.5): smooth and
+            # non-uniform in every block; pressure by Bernoulli, density
+            # isentropic; wall nodes at rest
+            a2 = 0.25 / (R * R)
+            ur = mach * (1.0 - a2) * np.cos(TH)
+            ut = -mach * (1.0 + a2) * np.sin(TH)
+            u = ur * np.cos(TH) - ut * np.sin(TH)
+            v = ur * np.sin(TH) + ut * np.cos(TH)
+            p = 1.0 / g + 0.5 * (mach * mach - (u * u + v * v))
+            rho = (g * p) ** (1.0 / g)
             if l == 0:
-                u[:, 0, :] = 0.0   # wall nodes at rest
-            q = conservative(g, rho, u, 0.0, 0.0, 1.0 / g)
+                u[:, 0, :] = 0.0
+                v[:, 0, :] = 0.0
+            q = conservative(g, rho, u, v, 0.0, p)
             blocks.append(Block(xyz, faces, q))
             j0 += lay[l]
         i0 += sec[s]
