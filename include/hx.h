@@ -168,6 +168,32 @@ long long hx_points(const hx_ctx* ctx);
 /* Device bytes held by the context. */
 size_t hx_device_bytes(const hx_ctx* ctx);
 
+/* Residual R(Q) = dQ/dt of one block that is periodic on all six faces,
+ * Euler (inviscid terms only), FP64, computed without allocating any device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate -- code whose device memory is owned by another
+ * allocator (for example a framework's memory pool holding the whole GPU),
+ * or loops that must not call cudaMalloc/cudaFree because those calls can
+ * synchronise the device and take unbounded time.
+ *   q      device [5][nk][nj][ni] conservative state (rho, rho u, rho v, rho w, e)
+ *   met    device [10][nk][nj][ni] node metrics and J, as hx_get_metrics
+ *          returns them for that periodic block
+ *   r_out  device [5][nk][nj][ni], written
+ * The result equals hx_rhs of an FP64 Euler context holding that block with
+ * periodic faces, up to rounding.  All intermediates live in one static
+ * device array of 32 MiB that the library holds on every GPU it is loaded
+ * on until the process exits; a block whose padded fields do not fit (about
+ * 48^3 nodes and above) is rejected with HX_ERR_INVALID_ARG, as are extents
+ * below 6 and null pointers.  The first call on a device looks up that
+ * array's device address (a one-time set-up); make that first call before
+ * any stream capture.  Every call reuses the same array, so calls that
+ * overlap on the GPU (different streams or threads) race and corrupt each
+ * other's results; serialise them.  Work runs on cuda_stream (NULL = legacy
+ * default stream) and the call returns after that stream is idle.
+ * Returns HX_OK, HX_ERR_INVALID_ARG or HX_ERR_CUDA. */
+int hx_euler_rhs_periodic_noalloc(int ni, int nj, int nk, double gamma, const double* q, const double* met,
+                                  double* r_out, void* cuda_stream);
+
 /* Message of the last failure on ctx (or of the last hx_create failure when
  * ctx is NULL).  Valid until the next call on ctx. */
 const char* hx_last_error(const hx_ctx* ctx);

@@ -30,7 +30,7 @@ EXPORTS = (
     "hx_config_default", "hx_create", "hx_add_block", "hx_set_face", "hx_finalize", "hx_compute_metrics",
     "hx_set_state", "hx_get_state", "hx_get_metrics", "hx_compute_dt", "hx_step", "hx_step_multi", "hx_rhs",
     "hx_get_gradients", "hx_profile_step", "hx_launches_per_step", "hx_points", "hx_device_bytes",
-    "hx_last_error", "hx_destroy",
+    "hx_last_error", "hx_destroy", "hx_euler_rhs_periodic_noalloc",
 )
 
 
@@ -89,6 +89,7 @@ def load(path=None):
         "hx_device_bytes": (ctypes.c_size_t, [CTX]),
         "hx_last_error": (ctypes.c_char_p, [CTX]),
         "hx_destroy": (None, [CTX]),
+        "hx_euler_rhs_periodic_noalloc": (I, [I, I, I, D, VP, VP, VP, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -241,6 +242,26 @@ class Context:
     @property
     def device_bytes(self):
         return self._lib.hx_device_bytes(self._h)
+
+
+def euler_rhs_periodic_noalloc(q, met, r_out, gamma=1.4, stream=None):
+    """Residual of one fully periodic Euler block in FP64 without any device
+    allocation (hx_euler_rhs_periodic_noalloc); q [5][nk][nj][ni], met
+    [10][nk][nj][ni] and r_out [5][nk][nj][ni] are contiguous float64 CUDA
+    tensors.  For callers that cannot allocate device memory; see
+    include/hx.h for the size limit and the shared-scratch caveat."""
+    for t in (q, met, r_out):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise ValueError("q, met and r_out must be CUDA tensors")
+    _, nk, nj, ni = q.shape
+    _ptr(q, 5 * nk * nj * ni)
+    _ptr(met, 10 * nk * nj * ni)
+    _ptr(r_out, 5 * nk * nj * ni)
+    rc = load().hx_euler_rhs_periodic_noalloc(ni, nj, nk, float(gamma), q.data_ptr(), met.data_ptr(),
+                                              r_out.data_ptr(), ctypes.c_void_p(stream or 0))
+    if rc:
+        raise HxError(rc, "hx_euler_rhs_periodic_noalloc failed")
+    return r_out
 
 
 def from_workload(w, precision="fp64", stream=None, autotune=1, mem_cap_bytes=0):
