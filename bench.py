@@ -32,18 +32,20 @@ FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # Algorithmic work of one flux-sweep launch per interior node (one direction):
-# modified AFWENO inviscid part and, for Navier-Stokes, the viscous node flux
-# and its central derivative (counts derived operation by operation).
+# modified AFWENO inviscid part and, for Navier-Stokes, the projection of the
+# node stress tensor on the direction's metric and its central derivative
+# (counts derived operation by operation; the stress tensor itself is formed
+# once per node by the gradient kernel).
 FLUX_FLOPS_INV = 1060
-FLUX_FLOPS_VISC = 85
+FLUX_FLOPS_VISC = 50
 
 
 def flux_bytes_per_node(dir_, word, viscous):
     """Compulsory HBM bytes per node of one flux-sweep launch: the state (5),
     the metric of the direction (3), the accumulator (written by the xi sweep,
-    read and written by eta, zeta) and, for Navier-Stokes, primitives (4) and
-    gradients (12)."""
-    words = 5 + 3 + (5 if dir_ == 0 else 10) + (16 if viscous else 0)
+    read and written by eta, zeta) and, for Navier-Stokes, the node stress
+    tensor and work + heat-flux vector (9)."""
+    words = 5 + 3 + (5 if dir_ == 0 else 10) + (9 if viscous else 0)
     return words * word
 
 

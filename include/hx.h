@@ -150,8 +150,9 @@ int hx_step_multi(hx_ctx* ctx, int nsteps, const double* dt_per_block);
  * copies block `block`'s residual into r_out [5][nk][nj][ni]. */
 int hx_rhs(hx_ctx* ctx, int block, double* r_out, int on_device);
 
-/* After hx_rhs of a viscous context: copies the 12 node gradients
- * (u, v, w, T)_(x, y, z) of `block` into g_out [12][nk][nj][ni]. */
+/* Navier-Stokes only: forms the 12 node gradients (u, v, w, T)_(x, y, z) of
+ * the current state (Eq. (21)) and copies block `block`'s into
+ * g_out [12][nk][nj][ni]. */
 int hx_get_gradients(hx_ctx* ctx, int block, double* g_out, int on_device);
 
 /* Runs nsteps steps launch by launch (no graph) with CUDA events around each

@@ -59,10 +59,15 @@ __host__ __device__ inline long long node_index(const DevBlock& B, int i, int j,
 // ---------------------------------------------------------------------------
 // small math wrappers
 // ---------------------------------------------------------------------------
+// FP64: IEEE division and square root, CUDA's double rsqrt.  FP32 (mixed
+// form, 1e-5 error budget): the approximate hardware reciprocal and
+// reciprocal square root.
 __device__ __forceinline__ double hsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float hsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ float hsqrt(float x) { return x * rsqrtf(x); }
 __device__ __forceinline__ double hrcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float hrcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float hrcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double hrsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float hrsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double habs(double x) { return fabs(x); }
 __device__ __forceinline__ float habs(float x) { return fabsf(x); }
 __device__ __forceinline__ double hmax0(double x) { return fmax(x, 0.0); }
@@ -71,10 +76,10 @@ __device__ __forceinline__ double hmin0(double x) { return fmin(x, 0.0); }
 __device__ __forceinline__ float hmin0(float x) { return fminf(x, 0.0f); }
 
 template <class R>
-struct GasR {   // gas constants in the working precision
-    R gamma, gm1, inv_2gamma, two_gm1, c3g, mach_re, kq_fac, suth, one_p_suth;
+struct GasR {   // gas constants in the working precision (built on the host)
+    R gamma, gm1, inv_2gamma, two_gm1, c3g, mach_re, kq_fac, suth, one_p_suth, inv_gm1;
     int mu_law;
-    __device__ __forceinline__ void init(const Gas& g) {
+    __host__ __device__ void init(const Gas& g) {
         gamma = R(g.gamma);
         gm1 = R(g.gamma - 1.0);
         inv_2gamma = R(1.0 / (2.0 * g.gamma));
@@ -84,6 +89,7 @@ struct GasR {   // gas constants in the working precision
         kq_fac = R(1.0 / (g.pr * (g.gamma - 1.0)));
         suth = R(g.suth);
         one_p_suth = R(1.0 + g.suth);
+        inv_gm1 = R(1.0 / (g.gamma - 1.0));
         mu_law = g.mu_law;
     }
 };
@@ -139,8 +145,10 @@ __device__ __forceinline__ void weno_pair(double w0, double w1, double w2, doubl
     const double uR3 = 0.375 * w2 + 0.75 * w1 - 0.125 * w0;
     const double tL1 = 0.0625 * p23, tL2 = 0.625 * p13, tL3 = 0.3125 * p12;
     const double tR1 = 0.0625 * p12, tR2 = 0.625 * p13, tR3 = 0.3125 * p23;
-    left = (tL1 * uL1 + tL2 * uL2 + tL3 * uL3) / (tL1 + tL2 + tL3);
-    right = (tR1 * uR1 + tR2 * uR2 + tR3 * uR3) / (tR1 + tR2 + tR3);
+    const double dL = tL1 + tL2 + tL3, dR = tR1 + tR2 + tR3;
+    const double inv = 1.0 / (dL * dR);   // one division for both weight sets
+    left = (tL1 * uL1 + tL2 * uL2 + tL3 * uL3) * (dR * inv);
+    right = (tR1 * uR1 + tR2 * uR2 + tR3 * uR3) * (dL * inv);
 }
 
 __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3, float w4, float& left,
@@ -153,7 +161,7 @@ __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3
     const float b2 = (13.0f / 12.0f) * a2 * a2 + 0.25f * c2 * c2;
     const float b3 = (13.0f / 12.0f) * a3 * a3 + 0.25f * c3 * c3;
     // reciprocal form: no overflow of products of squared indicators in FP32
-    float r1 = __frcp_rn(eps + b1), r2 = __frcp_rn(eps + b2), r3 = __frcp_rn(eps + b3);
+    float r1 = __fdividef(1.0f, eps + b1), r2 = __fdividef(1.0f, eps + b2), r3 = __fdividef(1.0f, eps + b3);
     r1 *= r1;
     r2 *= r2;
     r3 *= r3;
@@ -165,8 +173,8 @@ __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3
     const float uR3 = 0.375f * w2 + 0.75f * w1 - 0.125f * w0;
     const float tL1 = 0.0625f * r1, tL2 = 0.625f * r2, tL3 = 0.3125f * r3;
     const float tR1 = 0.0625f * r3, tR2 = 0.625f * r2, tR3 = 0.3125f * r1;
-    left = (tL1 * uL1 + tL2 * uL2 + tL3 * uL3) * __frcp_rn(tL1 + tL2 + tL3);
-    right = (tR1 * uR1 + tR2 * uR2 + tR3 * uR3) * __frcp_rn(tR1 + tR2 + tR3);
+    left = __fdividef(tL1 * uL1 + tL2 * uL2 + tL3 * uL3, tL1 + tL2 + tL3);
+    right = __fdividef(tR1 * uR1 + tR2 * uR2 + tR3 * uR3, tR1 + tR2 + tR3);
 }
 
 // ---------------------------------------------------------------------------
@@ -184,7 +192,7 @@ __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3
 // ---------------------------------------------------------------------------
 template <class R>
 struct CharBasis {
-    R kx, ky, kz, u, v, w, rho, irho, c, a0, g, cir, al, half_uu, H, cth;
+    R kx, ky, kz, u, v, w, rho, irho, p, c, a0, g, cir, al, half_uu, H, cth;
     __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
         irho = hrcp(q[0]);
         rho = q[0];
@@ -192,11 +200,11 @@ struct CharBasis {
         v = q[2] * irho;
         w = q[3] * irho;
         half_uu = R(0.5) * (u * u + v * v + w * w);
-        const R p = gs.gm1 * (q[4] - rho * half_uu);
+        p = gs.gm1 * (q[4] - rho * half_uu);
         const R c2 = gs.gamma * p * irho;
-        c = hsqrt(c2);
-        const R ic = hrcp(c);
-        const R imm = hrcp(hsqrt(mx * mx + my * my + mz * mz));
+        const R ic = hrsqrt(c2);
+        c = c2 * ic;
+        const R imm = hrsqrt(mx * mx + my * my + mz * mz);
         kx = mx * imm;
         ky = my * imm;
         kz = mz * imm;
@@ -206,7 +214,7 @@ struct CharBasis {
         g = gs.gm1 * ic2;
         cir = c * irho * R(0.70710678118654752440);
         al = rho * ic * R(0.70710678118654752440);
-        H = half_uu + c2 / gs.gm1;
+        H = half_uu + c2 * gs.inv_gm1;
         cth = c * (kx * u + ky * v + kz * w);
     }
     // W = L q
@@ -261,7 +269,7 @@ __device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R kx, R
     const R uu = u * u + v * v + w * w;
     const R p = gs.gm1 * (q[4] - R(0.5) * q[0] * uu);
     const R c2 = gs.gamma * p * irho;
-    const R c = hsqrt(c2);
+    const R c = c2 * hrsqrt(c2);
     const R th = kx * u + ky * v + kz * w;
     R l1 = th * mm, l4 = (th + c) * mm, l5 = (th - c) * mm;
     if (POS) {
@@ -284,24 +292,28 @@ __device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R kx, R
     F[4] = a * (gs.gm1 * l1 * uu + R(0.5) * S45 * (uu + c2) + th * cD + S45 * c2 * gs.c3g);
 }
 
-// Viscous flux along metric m at a node, Eqs. (5)-(6): components 1..4
-// (the mass component is zero).  g = (u,v,w,T)_(x,y,z), row-major.
+// Stress tensor and work + heat-flux vector at a node, Eqs. (5)-(6) and the
+// definitions under Eq. (1): S = (tau_xx, tau_yy, tau_zz, tau_xy, tau_xz,
+// tau_yz, beta_x, beta_y, beta_z) from g = (u,v,w,T)_(x,y,z), row-major.  The
+// viscous flux of a direction with metric m is then (m.tau_x., m.tau_y.,
+// m.tau_z., m.beta): the direction-independent part is formed once per node.
 template <class R>
-__device__ __forceinline__ void viscous_flux(const GasR<R>& gs, R u, R v, R w, R T, const R g[12], R mx, R my,
-                                             R mz, R fv[4]) {
+__device__ __forceinline__ void stress(const GasR<R>& gs, R u, R v, R w, R T, const R g[12], R S[9]) {
     const R kv = gs.mach_re * viscosity(gs, T);
     const R kq = kv * gs.kq_fac;
     const R div = g[0] + g[4] + g[8];
     const R lam = R(-2.0 / 3.0) * kv * div;
     const R txx = lam + R(2) * kv * g[0], tyy = lam + R(2) * kv * g[4], tzz = lam + R(2) * kv * g[8];
     const R txy = kv * (g[1] + g[3]), txz = kv * (g[2] + g[6]), tyz = kv * (g[5] + g[7]);
-    const R bx = u * txx + v * txy + w * txz + kq * g[9];
-    const R by = u * txy + v * tyy + w * tyz + kq * g[10];
-    const R bz = u * txz + v * tyz + w * tzz + kq * g[11];
-    fv[0] = mx * txx + my * txy + mz * txz;
-    fv[1] = mx * txy + my * tyy + mz * tyz;
-    fv[2] = mx * txz + my * tyz + mz * tzz;
-    fv[3] = mx * bx + my * by + mz * bz;
+    S[0] = txx;
+    S[1] = tyy;
+    S[2] = tzz;
+    S[3] = txy;
+    S[4] = txz;
+    S[5] = tyz;
+    S[6] = u * txx + v * txy + w * txz + kq * g[9];
+    S[7] = u * txy + v * tyy + w * tyz + kq * g[10];
+    S[8] = u * txz + v * tyz + w * tzz + kq * g[11];
 }
 
 // Derivative at node p of a line of n nodes from values f(-4..4) around it,

@@ -25,10 +25,9 @@ FluxShape flux_shape(int dir, int v) {
 
 size_t flux_smem(bool fp64, int dir, int v, bool visc) {
     const FluxShape sh = flux_shape(dir, v);
-    const int NP = sh.tp + 6, NU = sh.tp + 2;
-    const size_t SP = dir == 0 ? (size_t)sh.na * (NP + 1) : (size_t)NP * sh.na;
-    const size_t SU = dir == 0 ? (size_t)sh.na * (NU + 1) : (size_t)NU * sh.na;
-    return (fp64 ? 8 : 4) * (8 * SP + 10 * SU + (visc ? 4 * SP : 0));
+    const int ring = sh.tp >= 8 ? 2 * sh.tp : 16;
+    const size_t plane = dir == 0 ? (size_t)sh.na * (ring + 1) : (size_t)ring * sh.na;
+    return (fp64 ? 8 : 4) * plane * (visc ? 27 : 23);
 }
 
 int flux_ctas_per_sm(bool fp64, int dir, int v, bool visc) {

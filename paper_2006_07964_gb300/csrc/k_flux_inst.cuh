@@ -19,6 +19,7 @@ struct FluxInst {
     static constexpr int TP = flux_tp(DIR, V), NA = flux_na(DIR, V);
     static constexpr size_t smem = FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC>();
     static int ctas() {
+        cudaFuncSetAttribute(k_flux<R, DIR, TP, NA, VISC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         auto kern = k_flux<R, DIR, TP, NA, VISC>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
             cudaGetLastError();
@@ -32,9 +33,11 @@ struct FluxInst {
         return nb;
     }
     static cudaError_t run(const FluxArgs& a, cudaStream_t s) {
+        GasR<R> gs;
+        gs.init(a.gas);
         k_flux<R, DIR, TP, NA, VISC><<<a.grid, TP * NA, smem, s>>>(
-            a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, a.fs, (const R*)a.prim, (const R*)a.grad,
-            (R*)a.A, a.accumulate, a.gas);
+            a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, a.fs, (const R*)a.stress, (R*)a.A,
+            a.accumulate, gs);
         return cudaGetLastError();
     }
 };

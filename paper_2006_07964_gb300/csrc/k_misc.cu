@@ -293,11 +293,13 @@ k_prim(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
 }
 
 // Eq. (21): (u, v, w, T)_(x, y, z) = J * sum_d m^_d (.)_(xi_d), derivatives
-// by the sixth-order operator or the physical-face closure.
-template <class R>
+// by the sixth-order operator or the physical-face closure.  STRESS: write
+// the node stress tensor and work + heat-flux vector (9 fields) that every
+// direction's viscous flux projects; otherwise the 12 gradients.
+template <class R, bool STRESS>
 __global__ void __launch_bounds__(kThreads)
 k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const R* __restrict__ prim,
-       const R* __restrict__ met, long long fs, R* __restrict__ grad) {
+       const R* __restrict__ met, long long fs, R* __restrict__ out, GasR<R> gs) {
     for (int t = blockIdx.x; t < nb; t += gridDim.x) {
         const Brick br = bricks[t];
         int i, j, k;
@@ -323,11 +325,21 @@ k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
         R m[9];
 #pragma unroll
         for (int c = 0; c < 9; ++c) m[c] = met[c * fs + e];
+        R g[12];
 #pragma unroll
         for (int v = 0; v < 4; ++v)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                grad[(v * 3 + c) * fs + e] = J * (m[c] * dc[v][0] + m[3 + c] * dc[v][1] + m[6 + c] * dc[v][2]);
+                g[v * 3 + c] = J * (m[c] * dc[v][0] + m[3 + c] * dc[v][1] + m[6 + c] * dc[v][2]);
+        if (STRESS) {
+            R S[9];
+            stress(gs, prim[e], prim[fs + e], prim[2 * fs + e], prim[3 * fs + e], g, S);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) out[c * fs + e] = S[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) out[c * fs + e] = g[c];
+        }
     }
 }
 
@@ -375,8 +387,8 @@ k_rk(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bloc
             if (Qf) Qf[c * fs + e] = (float)q[c];
         }
         if (!finite) atomicOr(flags, (unsigned)FLAG_NONFINITE);
-        else if (!(q[0] > 0.0) || !(q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0] > 0.0))
-            atomicOr(flags, (unsigned)FLAG_UNPHYSICAL);
+        else if (!(q[0] > 0.0) || !(q[4] * q[0] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) > 0.0))
+            atomicOr(flags, (unsigned)FLAG_UNPHYSICAL);   // rho <= 0 or p <= 0 (p rho / (gamma-1) = e rho - |rho u|^2/2)
     }
 }
 
@@ -519,15 +531,28 @@ cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, con
 }
 
 cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, const void* prim, const void* met,
-                        bool fp64, long long fs, void* grad, cudaStream_t s) {
+                        bool fp64, long long fs, void* out, bool stress_mode, Gas gas, cudaStream_t s) {
     if (nb <= 0) return cudaSuccess;
     const int g = grid_for((long long)nb * kThreads);
-    if (fp64)
-        k_grad<double><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const double*)prim, (const double*)met, fs,
-                                              (double*)grad);
-    else
-        k_grad<float><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)prim, (const float*)met, fs,
-                                             (float*)grad);
+    if (fp64) {
+        GasR<double> gs;
+        gs.init(gas);
+        if (stress_mode)
+            k_grad<double, true><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const double*)prim,
+                                                         (const double*)met, fs, (double*)out, gs);
+        else
+            k_grad<double, false><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const double*)prim,
+                                                          (const double*)met, fs, (double*)out, gs);
+    } else {
+        GasR<float> gs;
+        gs.init(gas);
+        if (stress_mode)
+            k_grad<float, true><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)prim, (const float*)met,
+                                                        fs, (float*)out, gs);
+        else
+            k_grad<float, false><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)prim, (const float*)met,
+                                                         fs, (float*)out, gs);
+    }
     return cudaGetLastError();
 }
 

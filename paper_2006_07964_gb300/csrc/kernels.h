@@ -15,8 +15,7 @@ struct FluxArgs {
     const void* Q;      // R, 5 fields
     const void* met;    // R, 10 fields
     long long fs;       // field stride (elements)
-    const void* prim;   // R, 4 fields (u, v, w, T), Navier-Stokes only
-    const void* grad;   // R, 12 fields, Navier-Stokes only
+    const void* stress; // R, 9 fields (tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, beta), Navier-Stokes only
     void* A;            // R, 5 fields, accumulated divergence
     int accumulate;
     Gas gas;
@@ -52,8 +51,10 @@ cudaError_t launch_metrics(const Brick* bricks, int nb, const DevBlock* cblocks,
 cudaError_t launch_cast(const double* src, float* dst, long long n, cudaStream_t s);
 cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, const void* Q, bool fp64,
                         long long fs, void* prim, Gas gas, cudaStream_t s);
+// Gradients (u,v,w,T)_(x,y,z) (12 fields, stress_mode = false) or the node
+// stress tensor and work + heat-flux vector (9 fields, stress_mode = true).
 cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, const void* prim, const void* met,
-                        bool fp64, long long fs, void* grad, cudaStream_t s);
+                        bool fp64, long long fs, void* out, bool stress_mode, Gas gas, cudaStream_t s);
 cudaError_t launch_rk(const Brick* bricks, int nb, const DevBlock* blocks, const double* Qn, const double* Qk,
                       const void* A, bool fp64, const double* met, long long fs, double* Qout, float* Qf,
                       double ca, double cb, double cc, double gm1, unsigned* flags, cudaStream_t s);

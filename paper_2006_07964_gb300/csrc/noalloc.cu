@@ -25,24 +25,23 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mu;
 std::vector<void*> g_addr;
 
-constexpr int kTP = 16, kNA = 16, kVariant = 1;   // tile shape of flux variant 1 in every direction
+constexpr int kNA = 16, kVariant = 1;   // flux variant 1: 16 nodes per chunk x 16 lines, every direction
 
 long long rup(long long v, long long m) { return (v + m - 1) / m * m; }
 
+// Line groups of the three sweeps (kNA lines each, sweep origin 0).
 __global__ void k_na_setup(DevBlock B, DevBlock* dB, Tile* tiles, int n0, int n1, int n2, int ni, int nj, int nk) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) *dB = B;
-    const int ti = (ni + kNA - 1) / kNA, tj = (nj + kTP - 1) / kTP, tk = (nk + kTP - 1) / kTP;
-    const int tj0 = (nj + kNA - 1) / kNA, ti0 = (ni + kTP - 1) / kTP;
-    if (t < n0) {   // xi sweep: tiles (i0 step TP, j0 step NA, k)
-        const int i0 = (t % ti0) * kTP, r = t / ti0;
-        tiles[t] = Tile{0, i0, (r % tj0) * kNA, r / tj0};
-    } else if (t < n0 + n1) {   // eta sweep: (i0 step NA, j0 step TP, k)
-        const int u = t - n0, i0 = (u % ti) * kNA, r = u / ti;
-        tiles[t] = Tile{0, i0, (r % tj) * kTP, r / tj};
-    } else if (t < n0 + n1 + n2) {   // zeta sweep: (i0 step NA, j, k0 step TP)
-        const int u = t - n0 - n1, i0 = (u % ti) * kNA, r = u / ti;
-        tiles[t] = Tile{0, i0, r / tk, (r % tk) * kTP};
+    const int gi = (ni + kNA - 1) / kNA, gj = (nj + kNA - 1) / kNA;
+    if (t < n0) {   // xi sweep: groups of j lines at each k
+        tiles[t] = Tile{0, 0, (t % gj) * kNA, t / gj};
+    } else if (t < n0 + n1) {   // eta sweep: groups of i lines at each k
+        const int u = t - n0;
+        tiles[t] = Tile{0, (u % gi) * kNA, 0, u / gi};
+    } else if (t < n0 + n1 + n2) {   // zeta sweep: groups of i lines at each j
+        const int u = t - n0 - n1;
+        tiles[t] = Tile{0, (u % gi) * kNA, u / gi, 0};
     }
 }
 
@@ -111,9 +110,9 @@ extern "C" int hx_euler_rhs_periodic_noalloc(int ni, int nj, int nk, double gamm
     B.sk = (int)sk;
     B.base = XOFF + G * sj + G * sk;
     const long long fs = rup(sk * (nk + 2 * G), 64);
-    const int n0 = nk * ((nj + kNA - 1) / kNA) * ((ni + kTP - 1) / kTP);
-    const int n1 = nk * ((nj + kTP - 1) / kTP) * ((ni + kNA - 1) / kNA);
-    const int n2 = nj * ((nk + kTP - 1) / kTP) * ((ni + kNA - 1) / kNA);
+    const int n0 = nk * ((nj + kNA - 1) / kNA);
+    const int n1 = nk * ((ni + kNA - 1) / kNA);
+    const int n2 = nj * ((ni + kNA - 1) / kNA);
     const size_t off_tiles = 256;
     const size_t off_q = rup(off_tiles + sizeof(Tile) * (size_t)(n0 + n1 + n2), 256);
     const size_t off_m = off_q + 5 * (size_t)fs * 8;
@@ -144,12 +143,14 @@ extern "C" int hx_euler_rhs_periodic_noalloc(int ni, int nj, int nk, double gamm
         a.Q = Qp;
         a.met = Mp;
         a.fs = fs;
-        a.prim = nullptr;
-        a.grad = nullptr;
+        a.stress = nullptr;
         a.A = A;
         a.accumulate = d > 0;   // the xi sweep overwrites what the last call left
         a.gas = Gas{gamma, 0.0, 1.0, 1.0, 0.0, 0, 0};
-        a.grid = nd[d] < 152 * 4 ? nd[d] : 152 * 4;
+        // sets the kernel's shared-memory opt-in (no allocation) and sizes the grid
+        const int cps = flux_ctas_per_sm(true, d, kVariant, false);
+        if (cps <= 0) return HX_ERR_CUDA;
+        a.grid = nd[d] < 152 * cps ? nd[d] : 152 * cps;
         if (launch_flux(true, d, kVariant, false, a, s) != cudaSuccess) return HX_ERR_CUDA;
     }
     k_na_out<<<1024, 256, 0, s>>>(B, fs, A, met, r_out);

@@ -230,22 +230,21 @@ void coord_halo_items(const hx_ctx* ctx, int d, std::vector<HaloItem>& out) {
     }
 }
 
+// Line groups of the sweep kernel of direction d: NA adjacent lines each,
+// origin at sweep index 0 (the kernel marches the whole line).
 void make_tiles(const hx_ctx* ctx, int d, FluxShape sh, std::vector<Tile>& out) {
     for (int b = 0; b < (int)ctx->blocks.size(); ++b) {
         const HostBlock& H = ctx->blocks[b];
         const int ni = H.n[0], nj = H.n[1], nk = H.n[2];
         if (d == 0) {
             for (int k = 0; k < nk; ++k)
-                for (int j = 0; j < nj; j += sh.na)
-                    for (int i = 0; i < ni; i += sh.tp) out.push_back(Tile{b, i, j, k});
+                for (int j = 0; j < nj; j += sh.na) out.push_back(Tile{b, 0, j, k});
         } else if (d == 1) {
             for (int k = 0; k < nk; ++k)
-                for (int j = 0; j < nj; j += sh.tp)
-                    for (int i = 0; i < ni; i += sh.na) out.push_back(Tile{b, i, j, k});
+                for (int i = 0; i < ni; i += sh.na) out.push_back(Tile{b, i, 0, k});
         } else {
             for (int j = 0; j < nj; ++j)
-                for (int k = 0; k < nk; k += sh.tp)
-                    for (int i = 0; i < ni; i += sh.na) out.push_back(Tile{b, i, j, k});
+                for (int i = 0; i < ni; i += sh.na) out.push_back(Tile{b, i, j, 0});
         }
     }
 }
@@ -297,11 +296,12 @@ int enqueue_rhs(hx_ctx* ctx, const double* Qin, Prof* pf) {
         HX_CK(launch_prim(ctx->d_prim, ctx->n_prim, ctx->d_blocks, Qs, f64, ctx->fs, ctx->prim, ctx->gas, s));
         if (pf) pf->end();
         if (pf) pf->begin(K_GRAD);
-        HX_CK(launch_grad(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, s));
+        HX_CK(launch_grad(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, true,
+                          ctx->gas, s));
         if (pf) pf->end();
         if (ctx->n_halo_g) {
             if (pf) pf->begin(K_HALO_GRAD);
-            HX_CK(launch_halo(ctx->d_halo_g, ctx->n_halo_g, ctx->grad, f64, ctx->fs, 12, M, ctx->gas, s));
+            HX_CK(launch_halo(ctx->d_halo_g, ctx->n_halo_g, ctx->grad, f64, ctx->fs, 9, M, ctx->gas, s));
             if (pf) pf->end();
         }
     }
@@ -314,8 +314,7 @@ int enqueue_rhs(hx_ctx* ctx, const double* Qin, Prof* pf) {
         a.Q = Qs;
         a.met = M;
         a.fs = ctx->fs;
-        a.prim = ctx->prim;
-        a.grad = ctx->grad;
+        a.stress = ctx->grad;
         a.A = ctx->A;
         a.accumulate = d > 0;
         a.gas = ctx->gas;
@@ -405,8 +404,7 @@ int autotune(hx_ctx* ctx) {
                 a.Q = stencil_state(ctx, ctx->Qn);
                 a.met = stencil_met(ctx);
                 a.fs = ctx->fs;
-                a.prim = ctx->prim;
-                a.grad = ctx->grad;
+                a.stress = ctx->grad;
                 a.A = ctx->A;
                 a.accumulate = 0;
                 a.gas = ctx->gas;
@@ -845,8 +843,19 @@ int hx_get_metrics(hx_ctx* ctx, int block, double* m_out, int on_device) {
 }
 
 int hx_get_gradients(hx_ctx* ctx, int block, double* g_out, int on_device) {
-    if (ctx && !ctx->cfg.viscous) return fail(ctx, HX_ERR_STATE, "gradients exist only for Navier-Stokes");
-    return get_field(ctx, block, ctx ? ctx->grad : nullptr, ctx ? ctx->fp64() : true, 12, g_out, on_device);
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (!ctx->cfg.viscous) return fail(ctx, HX_ERR_STATE, "gradients exist only for Navier-Stokes");
+    // the step keeps only the node stress tensor; the 12 gradients of the
+    // current state are formed here (they overwrite it until the next stage)
+    const bool f64 = ctx->fp64();
+    void* Qs = (void*)stencil_state(ctx, ctx->Qn);
+    const void* M = stencil_met(ctx);
+    if (ctx->n_halo_q) HX_CK(launch_halo(ctx->d_halo_q, ctx->n_halo_q, Qs, f64, ctx->fs, 5, M, ctx->gas, ctx->stream));
+    HX_CK(launch_prim(ctx->d_prim, ctx->n_prim, ctx->d_blocks, Qs, f64, ctx->fs, ctx->prim, ctx->gas, ctx->stream));
+    HX_CK(launch_grad(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, false, ctx->gas,
+                      ctx->stream));
+    return get_field(ctx, block, ctx->grad, f64, 12, g_out, on_device);
 }
 
 int hx_compute_dt(hx_ctx* ctx, double cfl, double* dt_global, double* dt_per_block) {
