@@ -38,6 +38,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # once per node by the gradient kernel).
 FLUX_FLOPS_INV = 1060
 FLUX_FLOPS_VISC = 50
+RK_FLOPS = 30   # R = -J A and the three-term combination, five components
 
 
 def flux_bytes_per_node(dir_, word, viscous):
@@ -138,10 +139,15 @@ def roofline_for(ctx, w, precision, steps, dt, peaks):
     npts = w.npts
     out = {"kernel": name, "launch_ms": tot / launches, "share": tot / sum(v[1] for v in stats.values())}
     if name.startswith("flux_"):
-        d = {"flux_xi": 0, "flux_eta": 1, "flux_zeta": 2}[name]
+        d = {"flux_xi": 0, "flux_eta": 1, "flux_zeta": 2, "flux_zeta_rk": 2}[name]
         word = 8 if precision == "fp64" else 4
         flops = (FLUX_FLOPS_INV + (FLUX_FLOPS_VISC if w.viscous else 0)) * npts
         bytes_ = flux_bytes_per_node(d, word, w.viscous) * npts
+        if name == "flux_zeta_rk":
+            # the fused stage reads A instead of read + write, and does the FP64
+            # RK3 combination: Q^n, Q^(k), J in, Q^(k+1) out (+ FP32 copy)
+            bytes_ += (-5 * word + 16 * 8 + (5 * 4 if precision == "mixed" else 0)) * npts
+            flops += RK_FLOPS * npts
         gbs = bytes_ / per_launch_s / 1e9
         tfl = flops / per_launch_s / 1e12
         alu_peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS

@@ -48,6 +48,23 @@ struct HaloItem {      // one ghost node: dst <- f(src, aux)
 
 enum : int { FLAG_NONFINITE = 1, FLAG_BAD_GRID = 2, FLAG_UNPHYSICAL = 4 };
 
+// The RK3 stage combination (Eq. (20)) fused into the last sweep:
+// Q_out = ca Q^n + cb Q^(k) + cc dt R, R = -J A, in FP64.
+struct RKArgs {
+    const double* Qn;     // Q^n (read at the node only)
+    const double* Qk;     // stage input Q^(k), FP64
+    const double* metd;   // FP64 metrics; field 9 is J
+    double* Qout;         // stage output, FP64
+    float* Qfout;         // FP32 copy of the stage output (mixed form) or null
+    double ca, cb, cc, gm1;
+    unsigned* flags;
+};
+
+// Non-finite test on the exponent bits (integer pipe, not the FP64 unit).
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+    return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
+}
+
 // HaloItem.mode: bits 0-3 kind, bits 4-5 direction, bit 6 side (1 = + face),
 // bits 8.. translation index (coordinates).
 enum : int { HM_COPY = 0, HM_WALL = 1, HM_FARFIELD = 2, HM_TRANSLATE = 3, HM_REFLECT = 4 };

@@ -52,11 +52,14 @@ struct FluxLayout {
     }
 };
 
-template <class R, int DIR, int TP, int NA, bool VISC>
+// RK (last sweep only): instead of storing A, finish R = -J (A + div) and
+// the RK3 stage combination at each output node (Eq. (20), FP64), with the
+// wall-node values and the non-finite / non-physical flags.
+template <class R, int DIR, int TP, int NA, bool VISC, bool RK>
 __global__ void __launch_bounds__(TP * NA)
 k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int ntiles,
        const R* __restrict__ Q, const R* __restrict__ met, long long fs, const R* __restrict__ stress,
-       R* __restrict__ A, int accumulate, GasR<R> gs) {
+       R* __restrict__ A, int accumulate, GasR<R> gs, RKArgs rk) {
     using LY = FluxLayout<DIR, TP, NA>;
     constexpr int PL = LY::PLANE;
     constexpr int NT = TP * NA;
@@ -108,6 +111,13 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     p += first;
                     if (a0 + a >= na || p > n + 2) continue;
                     const int s0 = LY::idx(p, a);
+                    const bool vnode = VISC && !((lo && p < 0) || (hi && p >= n));
+                    R S[9];
+                    if (vnode) {   // issued first; consumed after the node flux
+                        const long long e = e0 + p * sd + a * sa;
+#pragma unroll
+                        for (int f = 0; f < 9; ++f) S[f] = stress[f * fs + e];
+                    }
                     R q[5];
 #pragma unroll
                     for (int f = 0; f < 5; ++f) q[f] = sQ[f * PL + s0];
@@ -123,11 +133,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         sF[3 * PL + s0] = q[3] * th + mz * cb.p;
                         sF[4 * PL + s0] = (q[4] + cb.p) * th;
                     }
-                    if (VISC && !((lo && p < 0) || (hi && p >= n))) {
-                        const long long e = e0 + p * sd + a * sa;
-                        R S[9];
-#pragma unroll
-                        for (int f = 0; f < 9; ++f) S[f] = stress[f * fs + e];
+                    if (vnode) {
                         sFv[s0] = mx * S[0] + my * S[3] + mz * S[4];
                         sFv[PL + s0] = mx * S[3] + my * S[1] + mz * S[5];
                         sFv[2 * PL + s0] = mx * S[4] + my * S[5] + mz * S[2];
@@ -196,6 +202,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                 const int sp = LY::idx(p, a), sm1 = LY::idx(p - 1, a);
                 const int s1 = LY::idx(p + 1, a), s2 = LY::idx(p + 2, a), s3 = LY::idx(p + 3, a);
                 const int t1 = LY::idx(p - 1, a), t2 = LY::idx(p - 2, a), t3 = LY::idx(p - 3, a);
+                R dv[5];
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     const R* F = sF + k * PL;
@@ -206,7 +213,53 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         auto fv = [&](int s) { return Fv[LY::idx(p + s, a)]; };
                         div -= dline<R>(fv, p, n, lo, hi);
                     }
-                    A[k * fs + e] = accumulate ? A[k * fs + e] + div : div;
+                    dv[k] = accumulate ? A[k * fs + e] + div : div;
+                }
+                if (!RK) {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) A[k * fs + e] = dv[k];
+                } else {
+                    const double f = -rk.cc * B.dt * rk.metd[9 * fs + e];
+                    double qo[5];
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        double v = rk.ca * rk.Qn[k * fs + e] + f * (double)dv[k];
+                        if (rk.cb != 0.0) v += rk.cb * rk.Qk[k * fs + e];
+                        qo[k] = v;
+                    }
+                    if (B.wall) {   // node indices of this output (line groups start at sweep index 0)
+                        const int ni_ = DIR == 0 ? p : T.i0 + a;
+                        const int nj_ = DIR == 1 ? p : (DIR == 0 ? T.j0 + a : T.j0);
+                        const int nk_ = DIR == 2 ? p : T.k0;
+                        const bool on = ((B.wall & 1) && ni_ == 0) || ((B.wall & 2) && ni_ == B.n[0] - 1) ||
+                                        ((B.wall & 4) && nj_ == 0) || ((B.wall & 8) && nj_ == B.n[1] - 1) ||
+                                        ((B.wall & 16) && nk_ == 0) || ((B.wall & 32) && nk_ == B.n[2] - 1);
+                        if (on) {
+                            const double pw = rk.gm1 * (qo[4] - 0.5 * (qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) / qo[0]);
+                            qo[1] = qo[2] = qo[3] = 0.0;
+                            qo[4] = pw / rk.gm1;
+                        }
+                    }
+                    bool bad = false;
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        bad = bad || nonfinite_bits(qo[k]);
+                        rk.Qout[k * fs + e] = qo[k];
+                    }
+                    if (rk.Qfout) {
+                        float qf[5];
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            qf[k] = (float)qo[k];
+                            rk.Qfout[k * fs + e] = qf[k];
+                        }
+                        if (!bad && !(qf[0] > 0.0f && qf[4] * qf[0] - 0.5f * (qf[1] * qf[1] + qf[2] * qf[2] + qf[3] * qf[3]) > 0.0f))
+                            atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
+                    } else if (!bad && !(qo[0] > 0.0 &&
+                                         qo[4] * qo[0] - 0.5 * (qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) > 0.0)) {
+                        atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
+                    }
+                    if (bad) atomicOr(rk.flags, (unsigned)FLAG_NONFINITE);
                 }
             }
             // no barrier here: the next chunk's loads touch only state and

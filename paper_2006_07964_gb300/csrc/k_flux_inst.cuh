@@ -14,13 +14,13 @@ constexpr int flux_na(int dir, int v) { return dir == 0 ? (v == 0 ? 8 : v == 1 ?
 
 namespace {
 
-template <class R, int DIR, int V, bool VISC>
+template <class R, int DIR, int V, bool VISC, bool RK = false>
 struct FluxInst {
     static constexpr int TP = flux_tp(DIR, V), NA = flux_na(DIR, V);
     static constexpr size_t smem = FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC>();
     static int ctas() {
-        cudaFuncSetAttribute(k_flux<R, DIR, TP, NA, VISC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        auto kern = k_flux<R, DIR, TP, NA, VISC>;
+        cudaFuncSetAttribute(k_flux<R, DIR, TP, NA, VISC, RK>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        auto kern = k_flux<R, DIR, TP, NA, VISC, RK>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
             cudaGetLastError();
             return 0;
@@ -35,18 +35,29 @@ struct FluxInst {
     static cudaError_t run(const FluxArgs& a, cudaStream_t s) {
         GasR<R> gs;
         gs.init(a.gas);
-        k_flux<R, DIR, TP, NA, VISC><<<a.grid, TP * NA, smem, s>>>(
+        k_flux<R, DIR, TP, NA, VISC, RK><<<a.grid, TP * NA, smem, s>>>(
             a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, a.fs, (const R*)a.stress, (R*)a.A,
-            a.accumulate, gs);
+            a.accumulate, gs, a.rk);
         return cudaGetLastError();
     }
 };
 
 }  // namespace
 
-int HX_CAT3(flux_ctas_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc) {
+int HX_CAT3(flux_ctas_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc, bool rk) {
     using R = HX_FLUX_R;
     constexpr int D = HX_FLUX_DIR;
+    if (rk && D == 2) {
+        switch (v * 2 + (visc ? 1 : 0)) {
+            case 0: return FluxInst<R, D, 0, false, D == 2>::ctas();
+            case 1: return FluxInst<R, D, 0, true, D == 2>::ctas();
+            case 2: return FluxInst<R, D, 1, false, D == 2>::ctas();
+            case 3: return FluxInst<R, D, 1, true, D == 2>::ctas();
+            case 4: return FluxInst<R, D, 2, false, D == 2>::ctas();
+            case 5: return FluxInst<R, D, 2, true, D == 2>::ctas();
+        }
+        return 0;
+    }
     switch (v * 2 + (visc ? 1 : 0)) {
         case 0: return FluxInst<R, D, 0, false>::ctas();
         case 1: return FluxInst<R, D, 0, true>::ctas();
@@ -61,6 +72,17 @@ int HX_CAT3(flux_ctas_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc) {
 cudaError_t HX_CAT3(flux_run_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc, const FluxArgs& a, cudaStream_t s) {
     using R = HX_FLUX_R;
     constexpr int D = HX_FLUX_DIR;
+    if (a.fuse_rk && D == 2) {
+        switch (v * 2 + (visc ? 1 : 0)) {
+            case 0: return FluxInst<R, D, 0, false, D == 2>::run(a, s);
+            case 1: return FluxInst<R, D, 0, true, D == 2>::run(a, s);
+            case 2: return FluxInst<R, D, 1, false, D == 2>::run(a, s);
+            case 3: return FluxInst<R, D, 1, true, D == 2>::run(a, s);
+            case 4: return FluxInst<R, D, 2, false, D == 2>::run(a, s);
+            case 5: return FluxInst<R, D, 2, true, D == 2>::run(a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (v * 2 + (visc ? 1 : 0)) {
         case 0: return FluxInst<R, D, 0, false>::run(a, s);
         case 1: return FluxInst<R, D, 0, true>::run(a, s);

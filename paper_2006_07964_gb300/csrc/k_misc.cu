@@ -1,7 +1,8 @@
 // k_misc.cu -- point-parallel kernels of the RK stage and of set-up:
 // layout packing, halo gathers, conservative metrics (Eqs. (7)-(8)),
-// primitives, chain-rule gradients (Eq. (21)), the RK3 combination
-// (Eq. (20)), physical-face node values and the CFL time step.
+// primitives, chain-rule gradients and the node stress tensor (Eq. (21),
+// Eqs. (5)-(6)), physical-face node values and the CFL time step.  The RK3
+// combination (Eq. (20)) is fused into the last flux sweep.
 #include "kernels.h"
 
 namespace hx {
@@ -343,55 +344,6 @@ k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
     }
 }
 
-// ---------------------------------------------------------------- RK3 stage
-// Eq. (20) in FP64: Q_out = ca Q^n + cb Q^(k) + cc dt R, R = -J A (Eqs.
-// (2)-(3)); wall nodes then get u = 0, e = p/(gamma-1); the mixed form also
-// writes the FP32 copy the stencil kernels read.
-template <class R>
-__global__ void __launch_bounds__(kThreads)
-k_rk(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const double* Qn,
-     const double* Qk, const R* __restrict__ A, const double* __restrict__ met, long long fs, double* Qout,
-     float* Qf, double ca, double cb, double cc, double gm1, unsigned* flags) {
-    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
-        const Brick br = bricks[t];
-        int i, j, k;
-        bool ok;
-        brick_node(br, i, j, k, ok);
-        if (!ok) continue;
-        const DevBlock B = blocks[br.b];
-        const long long e = node_index(B, i, j, k);
-        const double f = -cc * B.dt * met[9 * fs + e];
-        double q[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            const double a = (double)A[c * fs + e];
-            double v = ca * Qn[c * fs + e] + f * a;
-            if (cb != 0.0) v += cb * Qk[c * fs + e];
-            q[c] = v;
-        }
-        if (B.wall) {
-            const bool on = ((B.wall & 1) && i == 0) || ((B.wall & 2) && i == B.n[0] - 1) ||
-                            ((B.wall & 4) && j == 0) || ((B.wall & 8) && j == B.n[1] - 1) ||
-                            ((B.wall & 16) && k == 0) || ((B.wall & 32) && k == B.n[2] - 1);
-            if (on) {
-                const double p = gm1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
-                q[1] = q[2] = q[3] = 0.0;
-                q[4] = p / gm1;
-            }
-        }
-        bool finite = true;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            finite = finite && isfinite(q[c]);
-            Qout[c * fs + e] = q[c];
-            if (Qf) Qf[c * fs + e] = (float)q[c];
-        }
-        if (!finite) atomicOr(flags, (unsigned)FLAG_NONFINITE);
-        else if (!(q[0] > 0.0) || !(q[4] * q[0] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) > 0.0))
-            atomicOr(flags, (unsigned)FLAG_UNPHYSICAL);   // rho <= 0 or p <= 0 (p rho / (gamma-1) = e rho - |rho u|^2/2)
-    }
-}
-
 // Residual R = -J A of one block, packed [5][nk][nj][ni].
 template <class R>
 __global__ void k_rhs_out(DevBlock B, const R* __restrict__ A, const double* __restrict__ met, long long fs,
@@ -553,20 +505,6 @@ cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, con
             k_grad<float, false><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)prim, (const float*)met,
                                                          fs, (float*)out, gs);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_rk(const Brick* bricks, int nb, const DevBlock* blocks, const double* Qn, const double* Qk,
-                      const void* A, bool fp64, const double* met, long long fs, double* Qout, float* Qf,
-                      double ca, double cb, double cc, double gm1, unsigned* flags, cudaStream_t s) {
-    if (nb <= 0) return cudaSuccess;
-    const int g = grid_for((long long)nb * kThreads);
-    if (fp64)
-        k_rk<double><<<g, kThreads, 0, s>>>(bricks, nb, blocks, Qn, Qk, (const double*)A, met, fs, Qout, Qf, ca, cb,
-                                            cc, gm1, flags);
-    else
-        k_rk<float><<<g, kThreads, 0, s>>>(bricks, nb, blocks, Qn, Qk, (const float*)A, met, fs, Qout, Qf, ca, cb,
-                                           cc, gm1, flags);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@ struct FluxArgs {
     int accumulate;
     Gas gas;
     int grid;           // CTAs of the persistent launch
+    int fuse_rk;        // zeta sweep only: finish R and the RK3 stage instead of storing A
+    RKArgs rk;
 };
 
 struct FluxShape {
@@ -29,8 +31,9 @@ struct FluxShape {
 constexpr int kFluxVariants = 3;
 FluxShape flux_shape(int dir, int variant);
 size_t flux_smem(bool fp64, int dir, int variant, bool visc);
-// CTAs per SM the variant can keep resident (0 if it cannot launch).
-int flux_ctas_per_sm(bool fp64, int dir, int variant, bool visc);
+// CTAs per SM the variant can keep resident (0 if it cannot launch); also
+// sets the kernel's shared-memory opt-in.
+int flux_ctas_per_sm(bool fp64, int dir, int variant, bool visc, bool rk = false);
 cudaError_t launch_flux(bool fp64, int dir, int variant, bool visc, const FluxArgs& a, cudaStream_t s);
 
 // ---- everything else (k_misc.cu) ----------------------------------------
@@ -55,9 +58,6 @@ cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, con
 // stress tensor and work + heat-flux vector (9 fields, stress_mode = true).
 cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, const void* prim, const void* met,
                         bool fp64, long long fs, void* out, bool stress_mode, Gas gas, cudaStream_t s);
-cudaError_t launch_rk(const Brick* bricks, int nb, const DevBlock* blocks, const double* Qn, const double* Qk,
-                      const void* A, bool fp64, const double* met, long long fs, double* Qout, float* Qf,
-                      double ca, double cb, double cc, double gm1, unsigned* flags, cudaStream_t s);
 cudaError_t launch_bc_nodes(const HaloItem* items, int n, double* Q, float* Qf, const double* met, long long fs,
                             Gas gas, cudaStream_t s);
 cudaError_t launch_dt(const Brick* bricks, int nb, const DevBlock* blocks, const double* Q, const double* met,

@@ -36,9 +36,9 @@ struct HostBlock {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
-enum Kind { K_HALO, K_PRIM, K_GRAD, K_HALO_GRAD, K_FLUX0, K_FLUX1, K_FLUX2, K_RK, K_BC, K_COUNT };
-const char* kKindName[K_COUNT] = {"halo_q", "primitives", "gradients", "halo_grad", "flux_xi",
-                                  "flux_eta", "flux_zeta", "rk_update", "bc_nodes"};
+enum Kind { K_HALO, K_PRIM, K_GRAD, K_HALO_GRAD, K_FLUX0, K_FLUX1, K_FLUX2, K_FLUX2RK, K_BC, K_COUNT };
+const char* kKindName[K_COUNT] = {"halo_q", "primitives", "stress", "halo_stress", "flux_xi",
+                                  "flux_eta", "flux_zeta", "flux_zeta_rk", "bc_nodes"};
 
 // Process-wide autotune cache: (precision, dir, viscous, shape class) -> variant.
 std::mutex g_tune_mu;
@@ -62,7 +62,8 @@ struct hx_ctx {
     std::vector<void*> allocs;
 
     double *met = nullptr, *Qn = nullptr, *Qa = nullptr, *Qb = nullptr, *stage = nullptr;
-    float *metf = nullptr, *Qf = nullptr;
+    float *metf = nullptr;
+    float* Qf[3] = {nullptr, nullptr, nullptr};   // mixed form: FP32 copies of Qn, Qa, Qb
     void *A = nullptr, *prim = nullptr, *grad = nullptr;
     DevBlock* d_blocks = nullptr;
     Tile* d_tiles[3][kFluxVariants] = {};
@@ -77,6 +78,7 @@ struct hx_ctx {
 
     int variant[3] = {0, 0, 0};
     int grid[3] = {1, 1, 1};
+    int grid_rk = 1;   // zeta sweep with the fused RK stage
     bool tuned = false;
 
     cudaGraphExec_t gexec = nullptr;
@@ -249,8 +251,11 @@ void make_tiles(const hx_ctx* ctx, int d, FluxShape sh, std::vector<Tile>& out) 
     }
 }
 
-const void* stencil_state(const hx_ctx* ctx, const double* Qin) {
-    return ctx->fp64() ? (const void*)Qin : (const void*)ctx->Qf;
+// State the stencil kernels read in stage buffer slot `slot` (0 = Q^n,
+// 1 = Q^(1), 2 = Q^(2)): the FP64 buffer itself, or its FP32 copy.
+void* stencil_state(const hx_ctx* ctx, int slot) {
+    double* q64[3] = {ctx->Qn, ctx->Qa, ctx->Qb};
+    return ctx->fp64() ? (void*)q64[slot] : (void*)ctx->Qf[slot];
 }
 const void* stencil_met(const hx_ctx* ctx) { return ctx->fp64() ? (const void*)ctx->met : (const void*)ctx->metf; }
 
@@ -279,12 +284,14 @@ struct Prof {
     }
 };
 
-// The residual of one stage: halo, (gradients), three flux sweeps into A.
-int enqueue_rhs(hx_ctx* ctx, const double* Qin, Prof* pf) {
+// The residual of one stage from stage slot `in`: halo, (stress tensor),
+// three flux sweeps.  rk == null: A holds the accumulated divergence.  With
+// rk, the zeta sweep finishes R = -J A and the RK3 stage into rk->Qout.
+int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf) {
     cudaStream_t s = ctx->stream;
     const bool f64 = ctx->fp64();
     const bool visc = ctx->cfg.viscous != 0;
-    void* Qs = (void*)stencil_state(ctx, Qin);
+    void* Qs = stencil_state(ctx, in);
     const void* M = stencil_met(ctx);
     if (ctx->n_halo_q) {
         if (pf) pf->begin(K_HALO);
@@ -319,7 +326,13 @@ int enqueue_rhs(hx_ctx* ctx, const double* Qin, Prof* pf) {
         a.accumulate = d > 0;
         a.gas = ctx->gas;
         a.grid = ctx->grid[d];
-        if (pf) pf->begin(K_FLUX0 + d);
+        const bool fuse = d == 2 && rk;
+        if (fuse) {
+            a.fuse_rk = 1;
+            a.rk = *rk;
+            a.grid = ctx->grid_rk;
+        }
+        if (pf) pf->begin(fuse ? K_FLUX2RK : K_FLUX0 + d);
         HX_CK(launch_flux(f64, d, v, visc, a, s));
         if (pf) pf->end();
     }
@@ -328,20 +341,26 @@ int enqueue_rhs(hx_ctx* ctx, const double* Qin, Prof* pf) {
 
 int enqueue_step(hx_ctx* ctx, Prof* pf) {
     static const double co[3][3] = {{1.0, 0.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
-    double* qin[3] = {ctx->Qn, ctx->Qa, ctx->Qb};
-    double* qout[3] = {ctx->Qa, ctx->Qb, ctx->Qn};
+    static const int in_slot[3] = {0, 1, 2}, out_slot[3] = {1, 2, 0};
+    double* q64[3] = {ctx->Qn, ctx->Qa, ctx->Qb};
     cudaStream_t s = ctx->stream;
     for (int st = 0; st < 3; ++st) {
-        int rc = enqueue_rhs(ctx, qin[st], pf);
+        RKArgs rk{};
+        rk.Qn = ctx->Qn;
+        rk.Qk = q64[in_slot[st]];
+        rk.metd = ctx->met;
+        rk.Qout = q64[out_slot[st]];
+        rk.Qfout = ctx->fp64() ? nullptr : ctx->Qf[out_slot[st]];
+        rk.ca = co[st][0];
+        rk.cb = co[st][1];
+        rk.cc = co[st][2];
+        rk.gm1 = ctx->gas.gamma - 1.0;
+        rk.flags = ctx->d_flags;
+        int rc = enqueue_rhs(ctx, in_slot[st], &rk, pf);
         if (rc) return rc;
-        if (pf) pf->begin(K_RK);
-        HX_CK(launch_rk(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->Qn, qin[st], ctx->A, ctx->fp64(), ctx->met,
-                        ctx->fs, qout[st], ctx->Qf, co[st][0], co[st][1], co[st][2], ctx->gas.gamma - 1.0,
-                        ctx->d_flags, s));
-        if (pf) pf->end();
         if (ctx->n_bc) {
             if (pf) pf->begin(K_BC);
-            HX_CK(launch_bc_nodes(ctx->d_bc, ctx->n_bc, qout[st], ctx->Qf, ctx->met, ctx->fs, ctx->gas, s));
+            HX_CK(launch_bc_nodes(ctx->d_bc, ctx->n_bc, rk.Qout, rk.Qfout, ctx->met, ctx->fs, ctx->gas, s));
             if (pf) pf->end();
         }
     }
@@ -401,7 +420,7 @@ int autotune(hx_ctx* ctx) {
                 a.blocks = ctx->d_blocks;
                 a.tiles = ctx->d_tiles[d][v];
                 a.ntiles = ctx->ntiles[d][v];
-                a.Q = stencil_state(ctx, ctx->Qn);
+                a.Q = stencil_state(ctx, 0);
                 a.met = stencil_met(ctx);
                 a.fs = ctx->fs;
                 a.stress = ctx->grad;
@@ -437,6 +456,12 @@ int autotune(hx_ctx* ctx) {
         const int cps = std::max(1, flux_ctas_per_sm(f64, d, ctx->variant[d], visc));
         ctx->grid[d] = (int)std::max<long long>(
             1, std::min<long long>(ctx->ntiles[d][ctx->variant[d]], (long long)cps * ctx->num_sms));
+    }
+    {   // the zeta sweep with the fused RK stage (attributes set here, before any capture)
+        const int cps = flux_ctas_per_sm(f64, 2, ctx->variant[2], visc, true);
+        if (cps <= 0) return fail(ctx, HX_ERR_CUDA, "the fused zeta sweep cannot launch on this device");
+        ctx->grid_rk = (int)std::max<long long>(
+            1, std::min<long long>(ctx->ntiles[2][ctx->variant[2]], (long long)cps * ctx->num_sms));
     }
     ctx->tuned = true;
     return HX_OK;
@@ -657,7 +682,8 @@ int hx_finalize(hx_ctx* ctx) {
         if ((rc = dalloc(ctx, &ctx->grad, 12 * fs * r))) return rc;
     }
     if (!ctx->fp64()) {
-        if ((rc = dalloc(ctx, (void**)&ctx->Qf, 5 * fs * 4))) return rc;
+        for (int q = 0; q < 3; ++q)
+            if ((rc = dalloc(ctx, (void**)&ctx->Qf[q], 5 * fs * 4))) return rc;
         if ((rc = dalloc(ctx, (void**)&ctx->metf, 10 * fs * 4))) return rc;
     }
     if ((rc = dalloc(ctx, (void**)&ctx->stage, (size_t)ctx->max_block_pts * 12 * 8))) return rc;
@@ -675,7 +701,7 @@ int hx_finalize(hx_ctx* ctx) {
         HX_CK(launch_fill(ctx->grad, ctx->fp64(), 12 * ctx->fs, 0.0, ctx->stream));
     }
     if (!ctx->fp64()) {
-        HX_CK(launch_fill(ctx->Qf, false, 5 * ctx->fs, 1.0, ctx->stream));
+        for (int q = 0; q < 3; ++q) HX_CK(launch_fill(ctx->Qf[q], false, 5 * ctx->fs, 1.0, ctx->stream));
         HX_CK(launch_fill(ctx->metf, false, 10 * ctx->fs, 1.0, ctx->stream));
     }
     // ---- work lists
@@ -741,7 +767,7 @@ int hx_finalize(hx_ctx* ctx) {
     if ((rc = upload(ctx, &ctx->d_halo_g, hg))) return rc;
     if ((rc = upload(ctx, &ctx->d_bc, bc))) return rc;
     HX_CK(cudaStreamSynchronize(ctx->stream));
-    ctx->launches_per_step = 3 * ((ctx->n_halo_q ? 1 : 0) + (visc ? 2 + (ctx->n_halo_g ? 1 : 0) : 0) + 3 + 1 +
+    ctx->launches_per_step = 3 * ((ctx->n_halo_q ? 1 : 0) + (visc ? 2 + (ctx->n_halo_g ? 1 : 0) : 0) + 3 +
                                   (ctx->n_bc ? 1 : 0));
     ctx->finalized = true;
     return HX_OK;
@@ -817,7 +843,7 @@ int hx_set_state(hx_ctx* ctx, int block, const double* q, int on_device) {
         HX_CK(cudaMemcpyAsync(ctx->stage, q, 5 * H.npts() * 8, cudaMemcpyHostToDevice, ctx->stream));
         src = ctx->stage;
     }
-    HX_CK(launch_unpack2(src, ctx->Qn, ctx->Qf, ctx->fs, H.dev, 5, ctx->stream));
+    HX_CK(launch_unpack2(src, ctx->Qn, ctx->Qf[0], ctx->fs, H.dev, 5, ctx->stream));
     HX_CK(cudaStreamSynchronize(ctx->stream));
     return HX_OK;
 }
@@ -849,7 +875,7 @@ int hx_get_gradients(hx_ctx* ctx, int block, double* g_out, int on_device) {
     // the step keeps only the node stress tensor; the 12 gradients of the
     // current state are formed here (they overwrite it until the next stage)
     const bool f64 = ctx->fp64();
-    void* Qs = (void*)stencil_state(ctx, ctx->Qn);
+    void* Qs = stencil_state(ctx, 0);
     const void* M = stencil_met(ctx);
     if (ctx->n_halo_q) HX_CK(launch_halo(ctx->d_halo_q, ctx->n_halo_q, Qs, f64, ctx->fs, 5, M, ctx->gas, ctx->stream));
     HX_CK(launch_prim(ctx->d_prim, ctx->n_prim, ctx->d_blocks, Qs, f64, ctx->fs, ctx->prim, ctx->gas, ctx->stream));
@@ -897,7 +923,7 @@ int hx_rhs(hx_ctx* ctx, int block, double* r_out, int on_device) {
     if (rc) return rc;
     if (block < 0 || block >= (int)ctx->blocks.size() || !r_out) return fail(ctx, HX_ERR_INVALID_ARG, "bad block or pointer");
     if ((rc = autotune(ctx))) return rc;
-    if ((rc = enqueue_rhs(ctx, ctx->Qn, nullptr))) return rc;
+    if ((rc = enqueue_rhs(ctx, 0, nullptr, nullptr))) return rc;
     const HostBlock& H = ctx->blocks[block];
     double* dst = on_device ? r_out : ctx->stage;
     HX_CK(launch_rhs_out(H.dev, ctx->A, ctx->fp64(), ctx->met, ctx->fs, dst, ctx->stream));

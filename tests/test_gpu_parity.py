@@ -206,7 +206,7 @@ def test_graph_replay_equals_profiled_launches():
     a.step(3, dt)
     stats = b.profile_step(3, dt)
     assert np.array_equal(a.get_state(0), b.get_state(0))
-    assert stats["flux_xi"][0] == 9 and stats["rk_update"][0] == 9
+    assert stats["flux_xi"][0] == 9 and stats["flux_zeta_rk"][0] == 9
 
 
 def test_checkpoint_resume_bitwise():
