@@ -101,6 +101,35 @@ class Clocks:
                 "samples": len(sm)}
 
 
+class Ranks:
+    """Replica bookkeeping for torchrun launches: every rank runs the whole
+    workload on its own GPU (the path keeps every block on one GPU, so there
+    is no data exchange); a barrier brackets the timed region and the job's
+    time is the maximum over ranks."""
+
+    def __init__(self, world):
+        self.world = world
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, x):
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(x)], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def throughput(self, npts, steps, seconds):
+        """Whole-job Mpts/s: all replicas' node RK-stage updates over the
+        slowest rank's time."""
+        return self.world * npts * 3 * steps / seconds / 1e6
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -247,18 +276,9 @@ def main():
     stream = torch.cuda.Stream()
     peaks = load_peaks()
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(world)
+    barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
     # time step from the FP64 state (held fixed, as the oracle does)
     probe = hx.from_workload(w, precision="fp64", stream=stream.cuda_stream)
@@ -277,7 +297,7 @@ def main():
     barrier()
     secs = max_over_ranks(secs)
     launches = ctx.launches_per_step * args.steps
-    value = world * w.npts * 3 * args.steps / secs / 1e6
+    value = ranks.throughput(w.npts, args.steps, secs)
     roof = roofline_for(ctx, w, head, 2, dt, peaks)
     ctx.close()
 
@@ -285,7 +305,7 @@ def main():
     if head == "fp64" and "mixed" in forms:
         msecs, mctx = run_form(torch, hx, w, "mixed", args.steps, args.warmup, stream, dt)
         msecs = max_over_ranks(msecs)
-        mval = world * w.npts * 3 * args.steps / msecs / 1e6
+        mval = ranks.throughput(w.npts, args.steps, msecs)
         mixed = {"value": mval, "ms_per_step": msecs / args.steps * 1e3, "ratio_vs_fp64": mval / value,
                  "dtype": "f32 state/fluxes/WENO, f64 metrics/RK", "gpu_launches": mctx.launches_per_step * args.steps,
                  "roofline": roofline_for(mctx, w, "mixed", 2, dt, peaks)}
@@ -311,7 +331,7 @@ def main():
             ectx.get_state(b, hout[b].numpy())
     e_secs = max_over_ranks(time.perf_counter() - t0)
     ectx.close()
-    e2e = {"value": world * w.npts * 3 * e_steps / e_secs / 1e6, "unit": "Mpts/s", "h2d_bytes_per_step": h2d,
+    e2e = {"value": ranks.throughput(w.npts, e_steps, e_secs), "unit": "Mpts/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d, "steps": e_steps}
 
     if rank != 0:

@@ -42,10 +42,13 @@ def build(force=False):
 
 
 def load():
+    """Loads liboracle.so (building it if needed).  HX_ORACLE_LIB names
+    another build of hx_oracle.c to load instead; the mutation tests use it
+    to run the pins against copies with planted mistakes."""
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    lib = ctypes.CDLL(os.environ.get("HX_ORACLE_LIB") or build())
     P, I, D, VP = ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_void_p
     sig = {
         "orc_new": (VP, [P]),

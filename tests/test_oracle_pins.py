@@ -280,3 +280,43 @@ def test_farfield_invariants(ops):
     uni = n @ [0.25 / 1.0, 0.05, 0.0]
     assert un + 2 * c / (G - 1) == pytest.approx(uni + 2 * ci / (G - 1), rel=1e-13)
     assert un - 2 * c / (G - 1) == pytest.approx(n @ [0.2, 0, 0] - 2 / (G - 1), rel=1e-13)
+
+
+# ---------------------------------------------------------------- viscous stress (Eq. (1), Eq. (6))
+
+def _stress_rows(ops, q, g):
+    """tau rows and beta from the viscous flux along the three unit metrics."""
+    rows, beta = [], []
+    for d in range(3):
+        m = np.zeros(3)
+        m[d] = 1.0
+        fv = ops.viscous_flux(q, g, m)
+        rows.append(fv[1:4])
+        beta.append(fv[4])
+    return np.array(rows), np.array(beta)
+
+
+def test_viscous_stress_is_symmetric_and_traceless():
+    """Eq. (1): tau_ij = mu(du_i/dx_j + du_j/dx_i - 2/3 delta_ij div u), a
+    symmetric deviatoric tensor (zero trace for any velocity gradient)."""
+    ops = oracle.Ops(gamma=G, mach=0.7, reynolds=13.0, viscous=True, mu_law=1)
+    for _ in range(10):
+        q = cons(RNG.uniform(0.5, 2.0), *RNG.normal(size=3), RNG.uniform(0.3, 2.0))
+        g = RNG.normal(size=12)
+        tau, _ = _stress_rows(ops, q, g)
+        scale = np.abs(tau).max()
+        assert np.allclose(tau, tau.T, atol=1e-14 * scale)
+        assert abs(np.trace(tau)) < 1e-14 * scale
+        assert scale > 1e-3
+
+
+def test_viscous_stress_vanishes_for_rigid_rotation():
+    """A rigid rotation (antisymmetric velocity gradient) and uniform T
+    produce no stress and no heat flux."""
+    ops = oracle.Ops(gamma=G, mach=0.7, reynolds=13.0, viscous=True, mu_law=1)
+    q = cons(1.2, 0.3, -0.4, 0.1, 0.8)
+    w = RNG.normal(size=3)
+    grad_u = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    g = np.concatenate([grad_u.ravel(), np.zeros(3)])
+    tau, beta = _stress_rows(ops, q, g)
+    assert np.abs(tau).max() < 1e-15 and np.abs(beta).max() < 1e-15
