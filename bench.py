@@ -216,6 +216,97 @@ def cpu_baseline(w, seconds_target=15.0):
             "kind": "oracle", "sample": "%d full RK3 step(s) of the %d-node workload, %.1f s" % (steps, w.npts, el)}
 
 
+def _rel_errors(a, b):
+    """Relative L2 and L-infinity of rho, rho u (vector) and E between two
+    states [5][...] (b is the reference)."""
+    out_l2, out_inf = {}, {}
+    for name, idx in (("rho", [0]), ("rho_u", [1, 2, 3]), ("E", [4])):
+        da, db = a[idx], b[idx]
+        out_l2[name] = float(np.sqrt(((da - db) ** 2).sum() / (db ** 2).sum()))
+        out_inf[name] = float(np.abs(da - db).max() / np.abs(db).max())
+    return out_l2, out_inf
+
+
+def precision_report(torch, hx, w, steps, warmup, stream):
+    """Mixed form against the FP64 form on the same workload, same dt, same
+    number of steps: throughput of each and the relative L2 / L-infinity
+    error of rho, rho u, E after the steps (the FP64 GPU path, checked
+    against the oracle at full size elsewhere, is the reference)."""
+    probe = hx.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+    dt, _ = probe.compute_dt(0.5)
+    probe.close()
+    res = {}
+    states = {}
+    for form in ("fp64", "mixed"):
+        ctx = hx.from_workload(w, precision=form, stream=stream.cuda_stream)
+        ctx.step(warmup, dt)          # warm-up, autotune, graph capture
+        for b, blk in enumerate(w.blocks):
+            ctx.set_state(b, blk.q0)  # restart from the initial state
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(steps, dt)
+        e1.record(stream)
+        e1.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        res[form] = {"mpts": w.npts * 3 * steps / secs / 1e6, "ms_per_step": secs / steps * 1e3}
+        states[form] = [ctx.get_state(b) for b in range(len(w.blocks))]
+        ctx.close()
+    a = np.concatenate([s.reshape(5, -1) for s in states["mixed"]], axis=1)
+    b = np.concatenate([s.reshape(5, -1) for s in states["fp64"]], axis=1)
+    l2, linf = _rel_errors(a, b)
+    return {"report": "precision", "workload": w.name, "points": w.npts, "steps": steps, "dt": dt,
+            "time": dt * steps, "fp64": res["fp64"], "mixed": res["mixed"],
+            "ratio_mixed_vs_fp64": res["mixed"]["mpts"] / res["fp64"]["mpts"],
+            "rel_l2_mixed_vs_fp64": l2, "rel_linf_mixed_vs_fp64": linf}
+
+
+def batch_report(torch, hx, w, steps, warmup, stream):
+    """Many uneven instances: all blocks in one context (one launch per
+    kernel family over the block / line-group work lists, the RK step in one
+    CUDA graph, per-instance dt) against one context per instance stepped one
+    after another, in both forms."""
+    from paper_2006_07964_gb300 import workloads as W
+    out = {"report": "batch", "workload": w.name, "instances": len(w.blocks), "points": w.npts, "steps": steps}
+    probe = hx.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+    _, dts = probe.compute_dt(0.5)
+    probe.close()
+    for form in ("fp64", "mixed"):
+        ctx = hx.from_workload(w, precision=form, stream=stream.cuda_stream)
+        ctx.step(warmup, dts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(steps, dts)
+        e1.record(stream)
+        e1.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        out["batched_" + form] = {"mpts": w.npts * 3 * steps / secs / 1e6, "launches_per_step": ctx.launches_per_step}
+        ctx.close()
+        singles = []
+        for b, blk in enumerate(w.blocks):
+            one = W.Workload(w.name + "_%d" % b, [W.Block(blk.xyz, [W.Face(f.kind, 0, f.nbr_face, f.translate)
+                                                                     for f in blk.faces], blk.q0)],
+                             gamma=w.gamma, mach=w.mach, reynolds=w.reynolds, prandtl=w.prandtl,
+                             viscous=w.viscous, mu_law=w.mu_law)
+            c = hx.from_workload(one, precision=form, stream=stream.cuda_stream)
+            c.step(warmup, dts[b])
+            singles.append(c)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for b, c in enumerate(singles):
+            c.step(steps, dts[b])
+        e1.record(stream)
+        e1.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        out["per_instance_" + form] = {"mpts": w.npts * 3 * steps / secs / 1e6,
+                                       "launches_per_step": sum(c.launches_per_step for c in singles)}
+        for c in singles:
+            c.close()
+    out["batched_mixed_vs_per_instance_fp64"] = out["batched_mixed"]["mpts"] / out["per_instance_fp64"]["mpts"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,6 +317,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--forms", default="fp64,mixed", help="comma list of fp64, mixed")
+    ap.add_argument("--report", choices=["precision", "batch"], default=None,
+                    help="print a precision (mixed vs FP64 errors) or batch (batched vs per-instance) report "
+                         "instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -275,6 +369,12 @@ def main():
     w = make(W)
     stream = torch.cuda.Stream()
     peaks = load_peaks()
+    if args.report == "precision":
+        print(json.dumps(precision_report(torch, hx, w, args.steps, args.warmup, stream)))
+        return
+    if args.report == "batch":
+        print(json.dumps(batch_report(torch, hx, w, args.steps, args.warmup, stream)))
+        return
 
     ranks = Ranks(world)
     barrier = ranks.barrier

@@ -56,6 +56,7 @@ struct RKArgs {
     const double* metd;   // FP64 metrics; field 9 is J
     double* Qout;         // stage output, FP64
     float* Qfout;         // FP32 copy of the stage output (mixed form) or null
+    const float* Aref;    // mixed form: the FP32 divergence of the rest state (rounding only), or null
     double ca, cb, cc, gm1;
     unsigned* flags;
 };

@@ -68,6 +68,14 @@ __global__ void k_pack(const T* __restrict__ src, long long fs, DevBlock B, int 
     }
 }
 
+// Fills fields [f0, f0 + nf) of an arena with per-field values v[f].
+template <class T>
+__global__ void k_fill_fields(T* p, long long fs, int nf, const double* __restrict__ v) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < fs * nf;
+         t += (long long)gridDim.x * blockDim.x)
+        p[t] = (T)v[t / fs];
+}
+
 template <class T>
 __global__ void k_fill(T* p, long long n, T v) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
@@ -346,8 +354,8 @@ k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
 
 // Residual R = -J A of one block, packed [5][nk][nj][ni].
 template <class R>
-__global__ void k_rhs_out(DevBlock B, const R* __restrict__ A, const double* __restrict__ met, long long fs,
-                          double* __restrict__ out) {
+__global__ void k_rhs_out(DevBlock B, const R* __restrict__ A, const float* __restrict__ Aref,
+                          const double* __restrict__ met, long long fs, double* __restrict__ out) {
     const long long N = (long long)B.n[0] * B.n[1] * B.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N * 5;
          t += (long long)gridDim.x * blockDim.x) {
@@ -356,7 +364,8 @@ __global__ void k_rhs_out(DevBlock B, const R* __restrict__ A, const double* __r
         const long long r2 = r / B.n[0];
         const int j = (int)(r2 % B.n[1]), k = (int)(r2 / B.n[1]);
         const long long e = node_index(B, i, j, k);
-        out[t] = -met[9 * fs + e] * (double)A[f * fs + e];
+        const R a = Aref ? A[f * fs + e] - (R)Aref[f * fs + e] : A[f * fs + e];
+        out[t] = -met[9 * fs + e] * (double)a;
     }
 }
 
@@ -431,6 +440,14 @@ cudaError_t launch_fill(void* p, bool fp64, long long n, double v, cudaStream_t 
         k_fill<double><<<grid_for(n), kThreads, 0, s>>>((double*)p, n, v);
     else
         k_fill<float><<<grid_for(n), kThreads, 0, s>>>((float*)p, n, (float)v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_fields(void* p, bool fp64, long long fs, int nf, const double* v, cudaStream_t s) {
+    if (fp64)
+        k_fill_fields<double><<<grid_for(fs * nf), kThreads, 0, s>>>((double*)p, fs, nf, v);
+    else
+        k_fill_fields<float><<<grid_for(fs * nf), kThreads, 0, s>>>((float*)p, fs, nf, v);
     return cudaGetLastError();
 }
 
@@ -515,13 +532,13 @@ cudaError_t launch_dt(const Brick* bricks, int nb, const DevBlock* blocks, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_rhs_out(DevBlock B, const void* A, bool fp64, const double* met, long long fs, double* out,
-                           cudaStream_t s) {
+cudaError_t launch_rhs_out(DevBlock B, const void* A, const float* Aref, bool fp64, const double* met, long long fs,
+                           double* out, cudaStream_t s) {
     const long long n = (long long)B.n[0] * B.n[1] * B.n[2] * 5;
     if (fp64)
-        k_rhs_out<double><<<grid_for(n), kThreads, 0, s>>>(B, (const double*)A, met, fs, out);
+        k_rhs_out<double><<<grid_for(n), kThreads, 0, s>>>(B, (const double*)A, nullptr, met, fs, out);
     else
-        k_rhs_out<float><<<grid_for(n), kThreads, 0, s>>>(B, (const float*)A, met, fs, out);
+        k_rhs_out<float><<<grid_for(n), kThreads, 0, s>>>(B, (const float*)A, Aref, met, fs, out);
     return cudaGetLastError();
 }
 

@@ -62,8 +62,10 @@ cudaError_t launch_bc_nodes(const HaloItem* items, int n, double* Q, float* Qf, 
                             Gas gas, cudaStream_t s);
 cudaError_t launch_dt(const Brick* bricks, int nb, const DevBlock* blocks, const double* Q, const double* met,
                       long long fs, Gas gas, unsigned long long* bmax, cudaStream_t s);
-cudaError_t launch_rhs_out(DevBlock B, const void* A, bool fp64, const double* met, long long fs, double* out,
-                           cudaStream_t s);
+cudaError_t launch_rhs_out(DevBlock B, const void* A, const float* Aref, bool fp64, const double* met, long long fs,
+                           double* out, cudaStream_t s);
+// Fills nf fields (field stride fs) with the per-field values v[0..nf) (device array).
+cudaError_t launch_fill_fields(void* p, bool fp64, long long fs, int nf, const double* v, cudaStream_t s);
 cudaError_t launch_fill(void* p, bool fp64, long long n, double v, cudaStream_t s);
 
 }  // namespace hx
