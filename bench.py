@@ -193,6 +193,7 @@ def roofline_for(ctx, w, precision, steps, dt, peaks):
                         "alu_view": {"achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac}})
     out["traffic"] = None
     out["per_kernel_ms"] = {k: v[1] / v[0] for k, v in stats.items()}
+    out["autotune"] = ctx.tuning()
     return out
 
 

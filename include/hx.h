@@ -160,6 +160,14 @@ int hx_get_gradients(hx_ctx* ctx, int block, double* g_out, int on_device);
  * out[0..*n_kinds-1] (at most max_kinds).  The state advances as in hx_step. */
 int hx_profile_step(hx_ctx* ctx, int nsteps, double dt, hx_kernel_stat* out, int max_kinds, int* n_kinds);
 
+/* The tile shapes the autotuner chose, after the first hx_step, hx_rhs or
+ * hx_profile_step (HX_ERR_STATE before).  variant[3] (may be NULL): chosen
+ * shape per direction (xi, eta, zeta); tile_shape[3][3][2] (may be NULL):
+ * (nodes per chunk along the sweep, lines per CTA) of each candidate;
+ * ms[3][3] (may be NULL): measured time of one launch per candidate, -1 where
+ * a candidate was not timed (cached choice, autotune off, or cannot launch). */
+int hx_tuning(const hx_ctx* ctx, int* variant, int* tile_shape, double* ms);
+
 /* Kernel launches one RK step makes (all stages). */
 int hx_launches_per_step(const hx_ctx* ctx);
 

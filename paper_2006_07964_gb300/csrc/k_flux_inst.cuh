@@ -9,8 +9,10 @@
 
 namespace hx {
 
-constexpr int flux_tp(int dir, int v) { return dir == 0 ? (v == 0 ? 32 : v == 1 ? 16 : 64) : (v == 0 ? 8 : 16); }
-constexpr int flux_na(int dir, int v) { return dir == 0 ? (v == 0 ? 8 : v == 1 ? 16 : 4) : (v == 0 ? 32 : v == 1 ? 16 : 32); }
+// Candidate (nodes per chunk, lines per CTA): xi (32,8) (16,16) (16,8);
+// eta and zeta (8,32) (16,16) (8,16).
+constexpr int flux_tp(int dir, int v) { return dir == 0 ? (v == 0 ? 32 : 16) : (v == 1 ? 16 : 8); }
+constexpr int flux_na(int dir, int v) { return dir == 0 ? (v == 0 ? 8 : v == 1 ? 16 : 8) : (v == 0 ? 32 : 16); }
 
 namespace {
 

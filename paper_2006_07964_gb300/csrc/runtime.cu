@@ -80,6 +80,7 @@ struct hx_ctx {
     int variant[3] = {0, 0, 0};
     int grid[3] = {1, 1, 1};
     int grid_rk = 1;   // zeta sweep with the fused RK stage
+    double tune_ms[3][kFluxVariants] = {{-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
     bool tuned = false;
 
     cudaGraphExec_t gexec = nullptr;
@@ -438,6 +439,7 @@ int autotune(hx_ctx* ctx) {
                 HX_CK(cudaEventSynchronize(e1));
                 float ms = 0;
                 HX_CK(cudaEventElapsedTime(&ms, e0, e1));
+                ctx->tune_ms[d][v] = ms / reps;
                 if (ms < best_ms) {
                     best_ms = ms;
                     best = v;
@@ -999,6 +1001,23 @@ int hx_profile_step(hx_ctx* ctx, int nsteps, double dt, hx_kernel_stat* out, int
 }
 
 int hx_launches_per_step(const hx_ctx* ctx) { return ctx ? ctx->launches_per_step : 0; }
+
+int hx_tuning(const hx_ctx* ctx, int* variant, int* tile_shape, double* ms) {
+    if (!ctx) return HX_ERR_INVALID_ARG;
+    if (!ctx->tuned) return HX_ERR_STATE;
+    for (int d = 0; d < 3; ++d) {
+        if (variant) variant[d] = ctx->variant[d];
+        for (int v = 0; v < kFluxVariants; ++v) {
+            if (tile_shape) {
+                const FluxShape sh = flux_shape(d, v);
+                tile_shape[(d * kFluxVariants + v) * 2] = sh.tp;
+                tile_shape[(d * kFluxVariants + v) * 2 + 1] = sh.na;
+            }
+            if (ms) ms[d * kFluxVariants + v] = ctx->tune_ms[d][v];
+        }
+    }
+    return HX_OK;
+}
 
 long long hx_points(const hx_ctx* ctx) {
     long long n = 0;

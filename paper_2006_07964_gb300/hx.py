@@ -30,7 +30,7 @@ EXPORTS = (
     "hx_config_default", "hx_create", "hx_add_block", "hx_set_face", "hx_finalize", "hx_compute_metrics",
     "hx_set_state", "hx_get_state", "hx_get_metrics", "hx_compute_dt", "hx_step", "hx_step_multi", "hx_rhs",
     "hx_get_gradients", "hx_profile_step", "hx_launches_per_step", "hx_points", "hx_device_bytes",
-    "hx_last_error", "hx_destroy", "hx_euler_rhs_periodic_noalloc",
+    "hx_last_error", "hx_destroy", "hx_euler_rhs_periodic_noalloc", "hx_tuning",
 )
 
 
@@ -90,6 +90,7 @@ def load(path=None):
         "hx_last_error": (ctypes.c_char_p, [CTX]),
         "hx_destroy": (None, [CTX]),
         "hx_euler_rhs_periodic_noalloc": (I, [I, I, I, D, VP, VP, VP, VP]),
+        "hx_tuning": (I, [CTX, ctypes.POINTER(I), ctypes.POINTER(I), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -230,6 +231,22 @@ class Context:
         n = ctypes.c_int()
         self._check(self._lib.hx_profile_step(self._h, int(nsteps), float(dt), out, 16, ctypes.byref(n)))
         return {out[i].name.decode(): (out[i].launches, out[i].total_ms) for i in range(n.value)}
+
+    def tuning(self):
+        """{direction: {"chosen": (tp, na), "candidates": {(tp, na): ms}}}."""
+        var = (ctypes.c_int * 3)()
+        shp = (ctypes.c_int * 18)()
+        ms = (ctypes.c_double * 9)()
+        self._check(self._lib.hx_tuning(self._h, var, shp, ms))
+        out = {}
+        for d, name in enumerate(("xi", "eta", "zeta")):
+            cands = {}
+            for v in range(3):
+                key = "%dx%d" % (shp[(d * 3 + v) * 2], shp[(d * 3 + v) * 2 + 1])
+                cands[key] = ms[d * 3 + v]
+            out[name] = {"chosen": "%dx%d" % (shp[(d * 3 + var[d]) * 2], shp[(d * 3 + var[d]) * 2 + 1]),
+                         "candidates_ms": cands}
+        return out
 
     @property
     def launches_per_step(self):
