@@ -26,6 +26,8 @@ struct DevBlock {
     long long base;   // element index of node (0, 0, 0) in the state layout
     int phys;         // bit f: face f is a physical face (wall or far field)
     int wall;         // bit f: face f is a wall
+    int ff;           // bit f: face f is a far field
+    int nbr[6];       // block joined across face f (periodic / interface), -1 on physical faces
     double dt;        // time step of this block
 };
 
@@ -44,6 +46,10 @@ struct Brick {         // box [i0, i0+ni) x [j0, j0+nj) x [k0, k0+nk) of block b
 
 struct HaloItem {      // one ghost node: dst <- f(src, aux)
     int dst, src, aux, mode;
+};
+
+struct NodeItem {      // a node on a physical face: block, indices, face direction and side
+    int b, i, j, k, dir, side, pad0, pad1;
 };
 
 enum : int { FLAG_NONFINITE = 1, FLAG_BAD_GRID = 2, FLAG_UNPHYSICAL = 4 };
@@ -73,6 +79,36 @@ enum : int { HM_COPY = 0, HM_WALL = 1, HM_FARFIELD = 2, HM_TRANSLATE = 3, HM_REF
 __host__ __device__ inline long long node_index(const DevBlock& B, int i, int j, int k) {
     return B.base + i + (long long)j * B.sj + (long long)k * B.sk;
 }
+
+// Halo by push: node id of block B sends its values `vals` (nf fields) to
+// the face ghosts they fill in the blocks joined across its faces (nodes
+// within G of a periodic or interface face), and, with `mirror`, to B's own
+// wall-mirror ghosts (nodes 1..G from a wall; fields 1..3, the momentum,
+// negated).  Each ghost has exactly one sender, so no synchronisation is
+// needed; the ghosts are ready for the next kernel on the stream.
+template <class T>
+__device__ __forceinline__ void push_ghosts(const DevBlock* __restrict__ blocks, const DevBlock& B, const int id[3],
+                                            T* arr, long long fs, int nf, const T* vals, bool mirror) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int d = f >> 1, side = f & 1;
+        const int s = side ? B.n[d] - 1 - id[d] : id[d];
+        int t[3] = {id[0], id[1], id[2]};
+        if (B.nbr[f] >= 0) {
+            if (s < G) {
+                const DevBlock& N = blocks[B.nbr[f]];
+                t[d] = side ? -1 - s : N.n[d] + s;
+                const long long e = node_index(N, t[0], t[1], t[2]);
+                for (int c = 0; c < nf; ++c) arr[c * fs + e] = vals[c];
+            }
+        } else if (mirror && ((B.wall >> f) & 1) && s >= 1 && s <= G) {
+            t[d] = side ? B.n[d] - 1 + s : -s;
+            const long long e = node_index(B, t[0], t[1], t[2]);
+            for (int c = 0; c < nf; ++c) arr[c * fs + e] = (c >= 1 && c <= 3) ? -vals[c] : vals[c];
+        }
+    }
+}
+
 
 // ---------------------------------------------------------------------------
 // small math wrappers
@@ -123,6 +159,19 @@ __device__ __forceinline__ R d6(R fm3, R fm2, R fm1, R fp1, R fp2, R fp3) {
 template <class R>
 __device__ __forceinline__ R mid6(R fm2, R fm1, R f0, R fp1, R fp2, R fp3) {
     return (R(3.0) * (fm2 + fp3) - R(25.0) * (fm1 + fp2) + R(150.0) * (f0 + fp1)) * R(1.0 / 256.0);
+}
+
+// Primitives (u, v, w, T) of a conservative state (T = gamma p / rho); the
+// one formula every kernel uses, so that results do not depend on which
+// kernel formed them.
+template <class R>
+__device__ __forceinline__ void primitives(const GasR<R>& gs, const R q[5], R pv[4]) {
+    const R irho = hrcp(q[0]);
+    pv[0] = q[1] * irho;
+    pv[1] = q[2] * irho;
+    pv[2] = q[3] * irho;
+    const R p = gs.gm1 * (q[4] - R(0.5) * (q[1] * pv[0] + q[2] * pv[1] + q[3] * pv[2]));
+    pv[3] = gs.gamma * p * irho;
 }
 
 // Viscosity: mu = 1, or Sutherland T^(3/2) (1+S)/(T+S).

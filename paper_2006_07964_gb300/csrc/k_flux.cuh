@@ -251,13 +251,14 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         rk.Qout[k * fs + e] = qo[k];
                     }
                     if (rk.Qfout) {
-                        float qf[5];
+                        float qv[5];
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
-                            qf[k] = (float)qo[k];
-                            rk.Qfout[k * fs + e] = qf[k];
+                            qv[k] = (float)qo[k];
+                            rk.Qfout[k * fs + e] = qv[k];
                         }
-                        if (!bad && !(qf[0] > 0.0f && qf[4] * qf[0] - 0.5f * (qf[1] * qf[1] + qf[2] * qf[2] + qf[3] * qf[3]) > 0.0f))
+                        if (!bad && !(qv[0] > 0.0f &&
+                                      qv[4] * qv[0] - 0.5f * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) > 0.0f))
                             atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
                     } else if (!bad && !(qo[0] > 0.0 &&
                                          qo[4] * qo[0] - 0.5 * (qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) > 0.0)) {

@@ -131,68 +131,95 @@ __device__ void farfield_state(const GasR<R>& gs, R mach, const R qi[5], R nx, R
 }
 
 // ---------------------------------------------------------------- halo
-// Ghost nodes of the state (face ghosts only): copy from the joined face's
-// node, wall mirror (rho, p even; velocity odd), or far-field state.
-template <class R>
-__global__ void k_halo(const HaloItem* __restrict__ items, int n, R* Q, long long fs, int nf,
-                       const R* __restrict__ met, Gas gas) {
-    GasR<R> gs;
+// Far-field faces after an RK stage: the boundary node gets the state of
+// the 1D characteristic rule from the updated node next to it (FP64), and
+// its FP32 copy in the mixed form.  Wall nodes are handled in the sweep.
+__global__ void k_bc_farfield(const NodeItem* __restrict__ items, int n, const DevBlock* __restrict__ blocks,
+                              double* Q, float* Qf, const double* __restrict__ met, long long fs, Gas gas) {
+    GasR<double> gs;
     gs.init(gas);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const HaloItem h = items[t];
-        const int kind = h.mode & 15;
-        if (kind == HM_COPY) {
-            for (int f = 0; f < nf; ++f) Q[f * fs + h.dst] = Q[f * fs + h.src];
-        } else if (kind == HM_WALL) {
-            Q[h.dst] = Q[h.src];
-            Q[fs + h.dst] = -Q[fs + h.src];
-            Q[2 * fs + h.dst] = -Q[2 * fs + h.src];
-            Q[3 * fs + h.dst] = -Q[3 * fs + h.src];
-            Q[4 * fs + h.dst] = Q[4 * fs + h.src];
-        } else if (kind == HM_FARFIELD) {
-            const int dir = (h.mode >> 4) & 3, side = (h.mode >> 6) & 1;
-            R m[3];
-            for (int c = 0; c < 3; ++c) m[c] = met[(3 * dir + c) * fs + h.aux];
-            const R sg = side ? R(1) : R(-1);
-            const R im = sg / hsqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-            R qi[5], qb[5];
-            for (int c = 0; c < 5; ++c) qi[c] = Q[c * fs + h.src];
-            farfield_state(gs, R(gas.mach), qi, m[0] * im, m[1] * im, m[2] * im, qb);
-            for (int c = 0; c < 5; ++c) Q[c * fs + h.dst] = qb[c];
+        const NodeItem it = items[t];
+        const DevBlock& B = blocks[it.b];
+        const int d = it.dir, side = it.side;
+        int in[3] = {it.i, it.j, it.k};
+        in[d] += side ? -1 : 1;
+        const long long e = node_index(B, it.i, it.j, it.k), ei = node_index(B, in[0], in[1], in[2]);
+        double m[3], qi[5], qb[5];
+        for (int c = 0; c < 3; ++c) m[c] = met[(3 * d + c) * fs + e];
+        const double im = (side ? 1.0 : -1.0) / sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+        for (int c = 0; c < 5; ++c) qi[c] = Q[c * fs + ei];
+        farfield_state(gs, gas.mach, qi, m[0] * im, m[1] * im, m[2] * im, qb);
+        for (int c = 0; c < 5; ++c) {
+            Q[c * fs + e] = qb[c];
+            if (Qf) Qf[c * fs + e] = (float)qb[c];
         }
     }
 }
 
-// Node values on physical faces after an RK stage: walls (u = 0,
-// e = p/(gamma-1)) in one launch, far fields (from the updated inward
-// node) in a second one.
-__global__ void k_bc_nodes(const HaloItem* __restrict__ items, int n, double* Q, float* Qf,
-                           const double* __restrict__ met, long long fs, Gas gas) {
-    GasR<double> gs;
+// Start of a stage: the ghost nodes of the stencil state and, for
+// Navier-Stokes, the primitives of every node the stress tensor reads, in
+// one pass over the bricks of the interior and of the six ghost slabs.  A
+// ghost takes the node of the joined block (periodic / interface), the
+// mirrored node (wall: rho, p even, velocity odd) or the far-field state of
+// the node next to the boundary; its primitives follow from its state.
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+k_prep(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, R* Q, long long fs,
+       const R* __restrict__ met, R* prim, Gas gas) {
+    GasR<R> gs;
     gs.init(gas);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const HaloItem h = items[t];
-        const int kind = h.mode & 15;
-        double qb[5];
-        if (kind == HM_WALL) {
-            double q[5];
-            for (int c = 0; c < 5; ++c) q[c] = Q[c * fs + h.dst];
-            const double irho = 1.0 / q[0];
-            const double p = gs.gm1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * irho);
-            qb[0] = q[0];
-            qb[1] = qb[2] = qb[3] = 0.0;
-            qb[4] = p / gs.gm1;
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const DevBlock& B = blocks[br.b];
+        const int id[3] = {i, j, k};
+        int d = -1;
+        for (int a = 0; a < 3; ++a)
+            if (id[a] < 0 || id[a] >= B.n[a]) d = a;
+        const long long e = node_index(B, i, j, k);
+        R q[5];
+        bool need_prim = prim != nullptr;
+        if (d < 0) {
+            for (int c = 0; c < 5; ++c) q[c] = Q[c * fs + e];
         } else {
-            const int dir = (h.mode >> 4) & 3, side = (h.mode >> 6) & 1;
-            double m[3], qi[5];
-            for (int c = 0; c < 3; ++c) m[c] = met[(3 * dir + c) * fs + h.aux];
-            const double im = (side ? 1.0 : -1.0) / sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-            for (int c = 0; c < 5; ++c) qi[c] = Q[c * fs + h.src];
-            farfield_state(gs, gas.mach, qi, m[0] * im, m[1] * im, m[2] * im, qb);
+            const int side = id[d] < 0 ? 0 : 1, f = 2 * d + side;
+            int src[3] = {i, j, k};
+            if (B.nbr[f] >= 0) {   // periodic / interface: the joined block's node
+                const DevBlock& N = blocks[B.nbr[f]];
+                src[d] = side ? id[d] - B.n[d] : id[d] + N.n[d];
+                const long long es = node_index(N, src[0], src[1], src[2]);
+                for (int c = 0; c < 5; ++c) q[c] = Q[c * fs + es];
+            } else if ((B.wall >> f) & 1) {   // wall mirror through the boundary node
+                src[d] = side ? 2 * (B.n[d] - 1) - id[d] : -id[d];
+                const long long es = node_index(B, src[0], src[1], src[2]);
+                for (int c = 0; c < 5; ++c) q[c] = Q[c * fs + es];
+                q[1] = -q[1];
+                q[2] = -q[2];
+                q[3] = -q[3];
+                need_prim = false;   // physical faces use one-sided viscous derivatives
+            } else {   // far field from the node next to the boundary node
+                int bn[3] = {i, j, k};
+                bn[d] = side ? B.n[d] - 1 : 0;
+                src[d] = side ? B.n[d] - 2 : 1;
+                const long long es = node_index(B, src[0], src[1], src[2]);
+                const long long eb = node_index(B, bn[0], bn[1], bn[2]);
+                R m[3], qi[5];
+                for (int c = 0; c < 3; ++c) m[c] = met[(3 * d + c) * fs + eb];
+                const R im = (side ? R(1) : R(-1)) / hsqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                for (int c = 0; c < 5; ++c) qi[c] = Q[c * fs + es];
+                farfield_state(gs, R(gas.mach), qi, m[0] * im, m[1] * im, m[2] * im, q);
+                need_prim = false;
+            }
+            for (int c = 0; c < 5; ++c) Q[c * fs + e] = q[c];
         }
-        for (int c = 0; c < 5; ++c) {
-            Q[c * fs + h.dst] = qb[c];
-            if (Qf) Qf[c * fs + h.dst] = (float)qb[c];
+        if (need_prim) {
+            R pv[4];
+            primitives(gs, q, pv);
+            for (int c = 0; c < 4; ++c) prim[c * fs + e] = pv[c];
         }
     }
 }
@@ -290,14 +317,10 @@ k_prim(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
         brick_node(br, i, j, k, ok);
         if (!ok) continue;
         const long long e = node_index(blocks[br.b], i, j, k);
-        const R q0 = Q[e], q1 = Q[fs + e], q2 = Q[2 * fs + e], q3 = Q[3 * fs + e], q4 = Q[4 * fs + e];
-        const R irho = hrcp(q0);
-        const R u = q1 * irho, v = q2 * irho, w = q3 * irho;
-        const R p = gs.gm1 * (q4 - R(0.5) * (q1 * u + q2 * v + q3 * w));
-        prim[e] = u;
-        prim[fs + e] = v;
-        prim[2 * fs + e] = w;
-        prim[3 * fs + e] = gs.gamma * p * irho;
+        R q[5], pv[4];
+        for (int c = 0; c < 5; ++c) q[c] = Q[c * fs + e];
+        primitives(gs, q, pv);
+        for (int c = 0; c < 4; ++c) prim[c * fs + e] = pv[c];
     }
 }
 
@@ -345,6 +368,7 @@ k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
             stress(gs, prim[e], prim[fs + e], prim[2 * fs + e], prim[3 * fs + e], g, S);
 #pragma unroll
             for (int c = 0; c < 9; ++c) out[c * fs + e] = S[c];
+            push_ghosts<R>(blocks, B, id, out, fs, 9, S, false);   // the stress halo of the sweeps
         } else {
 #pragma unroll
             for (int c = 0; c < 12; ++c) out[c * fs + e] = g[c];
@@ -456,16 +480,6 @@ cudaError_t launch_cast(const double* src, float* dst, long long n, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_halo(const HaloItem* items, int n, void* Q, bool fp64, long long fs, int nf, const void* met,
-                        Gas gas, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    if (fp64)
-        k_halo<double><<<grid_for(n), kThreads, 0, s>>>(items, n, (double*)Q, fs, nf, (const double*)met, gas);
-    else
-        k_halo<float><<<grid_for(n), kThreads, 0, s>>>(items, n, (float*)Q, fs, nf, (const float*)met, gas);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_halo_coords(const HaloItem* items, int n, double* X, long long fs, const double* tr,
                                cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
@@ -473,10 +487,22 @@ cudaError_t launch_halo_coords(const HaloItem* items, int n, double* X, long lon
     return cudaGetLastError();
 }
 
-cudaError_t launch_bc_nodes(const HaloItem* items, int n, double* Q, float* Qf, const double* met, long long fs,
-                            Gas gas, cudaStream_t s) {
+cudaError_t launch_bc_farfield(const NodeItem* items, int n, const DevBlock* blocks, double* Q, float* Qf,
+                               const double* met, long long fs, Gas gas, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_bc_nodes<<<grid_for(n), kThreads, 0, s>>>(items, n, Q, Qf, met, fs, gas);
+    k_bc_farfield<<<grid_for(n), kThreads, 0, s>>>(items, n, blocks, Q, Qf, met, fs, gas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const Brick* bricks, int nb, const DevBlock* blocks, void* Q, bool fp64, long long fs,
+                        const void* met, void* prim, Gas gas, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    const int g = grid_for((long long)nb * kThreads);
+    if (fp64)
+        k_prep<double><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (double*)Q, fs, (const double*)met, (double*)prim,
+                                              gas);
+    else
+        k_prep<float><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (float*)Q, fs, (const float*)met, (float*)prim, gas);
     return cudaGetLastError();
 }
 

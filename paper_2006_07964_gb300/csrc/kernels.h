@@ -45,8 +45,6 @@ cudaError_t launch_unpack2(const double* src, double* dst64, float* dst32, long 
                            cudaStream_t s);
 cudaError_t launch_pack(const void* src, bool src_fp64, long long fs, DevBlock B, int nf, double* dst,
                         cudaStream_t s);
-cudaError_t launch_halo(const HaloItem* items, int n, void* Q, bool fp64, long long fs, int nfields,
-                        const void* met, Gas gas, cudaStream_t s);
 cudaError_t launch_halo_coords(const HaloItem* items, int n, double* X, long long fs, const double* tr,
                                cudaStream_t s);
 cudaError_t launch_metrics(const Brick* bricks, int nb, const DevBlock* cblocks, const double* X, long long fsc,
@@ -58,8 +56,13 @@ cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, con
 // stress tensor and work + heat-flux vector (9 fields, stress_mode = true).
 cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, const void* prim, const void* met,
                         bool fp64, long long fs, void* out, bool stress_mode, Gas gas, cudaStream_t s);
-cudaError_t launch_bc_nodes(const HaloItem* items, int n, double* Q, float* Qf, const double* met, long long fs,
-                            Gas gas, cudaStream_t s);
+// Far-field boundary nodes after a stage.
+cudaError_t launch_bc_farfield(const NodeItem* items, int n, const DevBlock* blocks, double* Q, float* Qf,
+                               const double* met, long long fs, Gas gas, cudaStream_t s);
+// Ghosts of the stencil state and (prim != null) primitives over the bricks
+// of the interior and the ghost slabs.
+cudaError_t launch_prep(const Brick* bricks, int nb, const DevBlock* blocks, void* Q, bool fp64, long long fs,
+                        const void* met, void* prim, Gas gas, cudaStream_t s);
 cudaError_t launch_dt(const Brick* bricks, int nb, const DevBlock* blocks, const double* Q, const double* met,
                       long long fs, Gas gas, unsigned long long* bmax, cudaStream_t s);
 cudaError_t launch_rhs_out(DevBlock B, const void* A, const float* Aref, bool fp64, const double* met, long long fs,

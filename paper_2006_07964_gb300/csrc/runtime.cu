@@ -36,9 +36,9 @@ struct HostBlock {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
-enum Kind { K_HALO, K_PRIM, K_GRAD, K_HALO_GRAD, K_FLUX0, K_FLUX1, K_FLUX2, K_FLUX2RK, K_BC, K_COUNT };
-const char* kKindName[K_COUNT] = {"halo_q", "primitives", "stress", "halo_stress", "flux_xi",
-                                  "flux_eta", "flux_zeta", "flux_zeta_rk", "bc_nodes"};
+enum Kind { K_PREP, K_GRAD, K_FLUX0, K_FLUX1, K_FLUX2, K_FLUX2RK, K_BC, K_COUNT };
+const char* kKindName[K_COUNT] = {"prep", "stress", "flux_xi", "flux_eta", "flux_zeta", "flux_zeta_rk",
+                                  "bc_farfield"};
 
 // Process-wide autotune cache: (precision, dir, viscous, shape class) -> variant.
 std::mutex g_tune_mu;
@@ -71,8 +71,10 @@ struct hx_ctx {
     int ntiles[3][kFluxVariants] = {};
     Brick *d_int = nullptr, *d_prim = nullptr;
     int n_int = 0, n_prim = 0;
-    HaloItem *d_halo_q = nullptr, *d_halo_g = nullptr, *d_bc = nullptr;
-    int n_halo_q = 0, n_halo_g = 0, n_bc = 0;
+    NodeItem* d_bc = nullptr;       // far-field boundary nodes
+    int n_bc = 0;
+    Brick *d_ghost = nullptr, *d_prep = nullptr;   // ghost slabs; interior + ghost slabs
+    int n_ghost = 0, n_prep = 0;
     unsigned* d_flags = nullptr;
     unsigned long long* d_bmax = nullptr;
     long long max_block_pts = 0;
@@ -148,48 +150,6 @@ void add_bricks(std::vector<Brick>& out, int b, const int lo[3], const int hi[3]
         for (int j = lo[1]; j < hi[1]; j += 8)
             for (int i = lo[0]; i < hi[0]; i += 32)
                 out.push_back(Brick{b, i, j, k, std::min(32, hi[0] - i), std::min(8, hi[1] - j), 1, 0});
-}
-
-// Face ghost items of the state (or of the gradients when copies_only).
-void state_halo_items(const hx_ctx* ctx, bool copies_only, std::vector<HaloItem>& out) {
-    for (int b = 0; b < (int)ctx->blocks.size(); ++b) {
-        const HostBlock& H = ctx->blocks[b];
-        for (int f = 0; f < 6; ++f) {
-            const HostFace& F = H.f[f];
-            const bool phys = is_phys(F.kind);
-            if (copies_only && phys) continue;
-            const int d = f / 2, side = f % 2, a1 = (d + 1) % 3, a2 = (d + 2) % 3;
-            const int n = H.n[d];
-            for (int s = 1; s <= G; ++s)
-                for (int t2 = 0; t2 < H.n[a2]; ++t2)
-                    for (int t1 = 0; t1 < H.n[a1]; ++t1) {
-                        int g[3], src[3];
-                        g[d] = side ? n - 1 + s : -s;
-                        g[a1] = src[a1] = t1;
-                        g[a2] = src[a2] = t2;
-                        HaloItem it{};
-                        it.dst = (int)nidx(H.dev, g);
-                        if (!phys) {
-                            const HostBlock& N = ctx->blocks[F.nbr];
-                            src[d] = side ? s - 1 : N.n[d] - s;
-                            it.src = (int)nidx(N.dev, src);
-                            it.mode = HM_COPY;
-                        } else if (F.kind == HX_FACE_WALL) {
-                            src[d] = side ? n - 1 - s : s;
-                            it.src = (int)nidx(H.dev, src);
-                            it.mode = HM_WALL;
-                        } else {
-                            src[d] = side ? n - 2 : 1;
-                            it.src = (int)nidx(H.dev, src);
-                            int bn[3] = {g[0], g[1], g[2]};
-                            bn[d] = side ? n - 1 : 0;
-                            it.aux = (int)nidx(H.dev, bn);
-                            it.mode = HM_FARFIELD | (d << 4) | (side << 6);
-                        }
-                        out.push_back(it);
-                    }
-        }
-    }
 }
 
 // Coordinate ghost items of pass d (directions < d already carry ghosts).
@@ -286,33 +246,30 @@ struct Prof {
     }
 };
 
-// The residual of one stage from stage slot `in`: halo, (stress tensor),
-// three flux sweeps.  rk == null: A holds the accumulated divergence.  With
-// rk, the zeta sweep finishes R = -J A and the RK3 stage into rk->Qout.
-int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool halo = true) {
+// The residual of one stage from stage slot `in`: the ghosts of the
+// stencil state and the primitives (prep), the node stress tensor (pushing
+// its halo), then the three flux sweeps.  rk == null: A holds the
+// accumulated divergence.  With rk, the zeta sweep finishes R = -J A and
+// the RK3 stage into rk->Qout.
+int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = true) {
     cudaStream_t s = ctx->stream;
     const bool f64 = ctx->fp64();
     const bool visc = ctx->cfg.viscous != 0;
     void* Qs = stencil_state(ctx, in);
     const void* M = stencil_met(ctx);
-    if (ctx->n_halo_q && halo) {
-        if (pf) pf->begin(K_HALO);
-        HX_CK(launch_halo(ctx->d_halo_q, ctx->n_halo_q, Qs, f64, ctx->fs, 5, M, ctx->gas, s));
+    if (prep) {
+        if (pf) pf->begin(K_PREP);
+        if (visc)
+            HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, ctx->gas, s));
+        else
+            HX_CK(launch_prep(ctx->d_ghost, ctx->n_ghost, ctx->d_blocks, Qs, f64, ctx->fs, M, nullptr, ctx->gas, s));
         if (pf) pf->end();
     }
     if (visc) {
-        if (pf) pf->begin(K_PRIM);
-        HX_CK(launch_prim(ctx->d_prim, ctx->n_prim, ctx->d_blocks, Qs, f64, ctx->fs, ctx->prim, ctx->gas, s));
-        if (pf) pf->end();
         if (pf) pf->begin(K_GRAD);
         HX_CK(launch_grad(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, true,
                           ctx->gas, s));
         if (pf) pf->end();
-        if (ctx->n_halo_g && halo) {
-            if (pf) pf->begin(K_HALO_GRAD);
-            HX_CK(launch_halo(ctx->d_halo_g, ctx->n_halo_g, ctx->grad, f64, ctx->fs, 9, M, ctx->gas, s));
-            if (pf) pf->end();
-        }
     }
     for (int d = 0; d < 3; ++d) {
         const int v = ctx->variant[d];
@@ -363,7 +320,8 @@ int enqueue_step(hx_ctx* ctx, Prof* pf) {
         if (rc) return rc;
         if (ctx->n_bc) {
             if (pf) pf->begin(K_BC);
-            HX_CK(launch_bc_nodes(ctx->d_bc, ctx->n_bc, rk.Qout, rk.Qfout, ctx->met, ctx->fs, ctx->gas, s));
+            HX_CK(launch_bc_farfield(ctx->d_bc, ctx->n_bc, ctx->d_blocks, rk.Qout, rk.Qfout, ctx->met, ctx->fs,
+                                     ctx->gas, s));
             if (pf) pf->end();
         }
     }
@@ -517,6 +475,9 @@ int compute_ref_residual(hx_ctx* ctx) {
     if ((rc = dalloc(ctx, (void**)&dq, sizeof qref))) return rc;
     HX_CK(cudaMemcpyAsync(dq, qref, sizeof qref, cudaMemcpyHostToDevice, ctx->stream));
     HX_CK(launch_fill_fields(ctx->Qf[0], false, ctx->fs, 5, dq, ctx->stream));
+    if (ctx->cfg.viscous)
+        HX_CK(launch_prim(ctx->d_prim, ctx->n_prim, ctx->d_blocks, ctx->Qf[0], false, ctx->fs, ctx->prim, ctx->gas,
+                          ctx->stream));
     if ((rc = enqueue_rhs(ctx, 0, nullptr, nullptr, false))) return rc;
     HX_CK(cudaMemcpyAsync(ctx->Aref, ctx->A, 5 * (size_t)ctx->fs * 4, cudaMemcpyDeviceToDevice, ctx->stream));
     HX_CK(cudaStreamSynchronize(ctx->stream));
@@ -686,10 +647,12 @@ int hx_finalize(hx_ctx* ctx) {
         H.cdev.sk = (int)skc;
         H.cdev.base = offc + XOFF + GC * sjc + GC * skc;
         offc = round_up(offc + skc * (H.n[2] + 2 * GC), 32);
-        H.dev.phys = H.dev.wall = 0;
+        H.dev.phys = H.dev.wall = H.dev.ff = 0;
         for (int f = 0; f < 6; ++f) {
             if (is_phys(H.f[f].kind)) H.dev.phys |= 1 << f;
             if (H.f[f].kind == HX_FACE_WALL) H.dev.wall |= 1 << f;
+            if (H.f[f].kind == HX_FACE_FARFIELD) H.dev.ff |= 1 << f;
+            H.dev.nbr[f] = is_phys(H.f[f].kind) ? -1 : H.f[f].nbr;
         }
         H.dev.dt = 0.0;
         ctx->max_block_pts = std::max(ctx->max_block_pts, H.npts());
@@ -745,14 +708,12 @@ int hx_finalize(hx_ctx* ctx) {
             ctx->ntiles[d][v] = (int)t.size();
             if ((rc = upload(ctx, &ctx->d_tiles[d][v], t))) return rc;
         }
-    std::vector<Brick> bi, bp;
+    std::vector<Brick> bi, bp, bg;
     for (int b = 0; b < nb; ++b) {
         const HostBlock& H = ctx->blocks[b];
         const int lo[3] = {0, 0, 0}, hi[3] = {H.n[0], H.n[1], H.n[2]};
         add_bricks(bi, b, lo, hi);
-        add_bricks(bp, b, lo, hi);
-        for (int f = 0; f < 6; ++f) {
-            if (is_phys(H.f[f].kind)) continue;
+        for (int f = 0; f < 6; ++f) {   // face ghost slabs (no edges or corners)
             const int d = f / 2;
             int l2[3] = {0, 0, 0}, h2[3] = {H.n[0], H.n[1], H.n[2]};
             if (f % 2) {
@@ -762,16 +723,20 @@ int hx_finalize(hx_ctx* ctx) {
                 l2[d] = -G;
                 h2[d] = 0;
             }
-            add_bricks(bp, b, l2, h2);
+            add_bricks(bg, b, l2, h2);
         }
     }
+    bp = bi;
+    bp.insert(bp.end(), bg.begin(), bg.end());
     ctx->n_int = (int)bi.size();
     ctx->n_prim = (int)bp.size();
+    ctx->n_prep = (int)bp.size();
+    ctx->n_ghost = (int)bg.size();
     if ((rc = upload(ctx, &ctx->d_int, bi))) return rc;
     if ((rc = upload(ctx, &ctx->d_prim, bp))) return rc;
-    std::vector<HaloItem> hq, hg, bc;
-    state_halo_items(ctx, false, hq);
-    if (visc) state_halo_items(ctx, true, hg);
+    ctx->d_prep = ctx->d_prim;
+    if ((rc = upload(ctx, &ctx->d_ghost, bg))) return rc;
+    std::vector<NodeItem> bc;
     for (int b = 0; b < nb; ++b) {
         const HostBlock& H = ctx->blocks[b];
         for (int f = 0; f < 6; ++f) {
@@ -779,25 +744,18 @@ int hx_finalize(hx_ctx* ctx) {
             const int d = f / 2, side = f % 2, a1 = (d + 1) % 3, a2 = (d + 2) % 3;
             for (int t2 = 0; t2 < H.n[a2]; ++t2)
                 for (int t1 = 0; t1 < H.n[a1]; ++t1) {
-                    int id[3], in[3];
+                    int id[3];
                     id[d] = side ? H.n[d] - 1 : 0;
-                    id[a1] = in[a1] = t1;
-                    id[a2] = in[a2] = t2;
-                    in[d] = side ? H.n[d] - 2 : 1;
-                    bc.push_back(HaloItem{(int)nidx(H.dev, id), (int)nidx(H.dev, in), (int)nidx(H.dev, id),
-                                          HM_FARFIELD | (d << 4) | (side << 6)});
+                    id[a1] = t1;
+                    id[a2] = t2;
+                    bc.push_back(NodeItem{b, id[0], id[1], id[2], d, side, 0, 0});
                 }
         }
     }
-    ctx->n_halo_q = (int)hq.size();
-    ctx->n_halo_g = (int)hg.size();
     ctx->n_bc = (int)bc.size();
-    if ((rc = upload(ctx, &ctx->d_halo_q, hq))) return rc;
-    if ((rc = upload(ctx, &ctx->d_halo_g, hg))) return rc;
     if ((rc = upload(ctx, &ctx->d_bc, bc))) return rc;
     HX_CK(cudaStreamSynchronize(ctx->stream));
-    ctx->launches_per_step = 3 * ((ctx->n_halo_q ? 1 : 0) + (visc ? 2 + (ctx->n_halo_g ? 1 : 0) : 0) + 3 +
-                                  (ctx->n_bc ? 1 : 0));
+    ctx->launches_per_step = 3 * (1 + (visc ? 1 : 0) + 3 + (ctx->n_bc ? 1 : 0));
     ctx->finalized = true;
     return HX_OK;
 }
@@ -907,8 +865,7 @@ int hx_get_gradients(hx_ctx* ctx, int block, double* g_out, int on_device) {
     const bool f64 = ctx->fp64();
     void* Qs = stencil_state(ctx, 0);
     const void* M = stencil_met(ctx);
-    if (ctx->n_halo_q) HX_CK(launch_halo(ctx->d_halo_q, ctx->n_halo_q, Qs, f64, ctx->fs, 5, M, ctx->gas, ctx->stream));
-    HX_CK(launch_prim(ctx->d_prim, ctx->n_prim, ctx->d_blocks, Qs, f64, ctx->fs, ctx->prim, ctx->gas, ctx->stream));
+    HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, ctx->gas, ctx->stream));
     HX_CK(launch_grad(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, false, ctx->gas,
                       ctx->stream));
     return get_field(ctx, block, ctx->grad, f64, 12, g_out, on_device);
