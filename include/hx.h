@@ -146,6 +146,20 @@ int hx_step(hx_ctx* ctx, int nsteps, double dt);
 /* As hx_step with one time step per block (independent instances). */
 int hx_step_multi(hx_ctx* ctx, int nsteps, const double* dt_per_block);
 
+/* Advances every block nsteps TVD-RK3 steps with the time step chosen on
+ * the device at the start of every step from the current state (the CFL
+ * reduction of hx_compute_dt; Sec. 4.5.3 reduces the time step on the GPU
+ * as well): dt = cfl / max over all nodes (per_block = 0), or per block
+ * (per_block = 1, independent instances).  No host round trip per step; the
+ * step and its dt reduction are one CUDA graph.  *time_advanced (may be
+ * NULL) gets the sum of the global dt over the steps. */
+int hx_step_cfl(hx_ctx* ctx, int nsteps, double cfl, int per_block, double* time_advanced);
+
+/* Root-mean-square residual of the current state over all nodes of all
+ * blocks, per conservative variable: rms[c] = sqrt(sum R_c^2 / N)
+ * (Fig. 2 calc_res; reduced on the device, Sec. 4.5.3).  rms has 5 entries. */
+int hx_residual(hx_ctx* ctx, double* rms);
+
 /* Evaluates R(Q) = dQ/dt of the current state without advancing it and
  * copies block `block`'s residual into r_out [5][nk][nj][ni]. */
 int hx_rhs(hx_ctx* ctx, int block, double* r_out, int on_device);

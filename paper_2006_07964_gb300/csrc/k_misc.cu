@@ -428,9 +428,74 @@ k_dt(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bloc
     }
 }
 
+// dt of every block from the per-block maxima of k_dt: cfl / max (global
+// minimum when per_block == 0), written into the block table; the global dt
+// is added to the simulated-time accumulator.
+__global__ void k_setdt(DevBlock* blocks, int nb, const unsigned long long* __restrict__ bmax,
+                        const double* __restrict__ cfl, int per_block, double* time_acc, unsigned* flags) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double gmax = 0.0;
+    for (int b = 0; b < nb; ++b) gmax = fmax(gmax, __longlong_as_double((long long)bmax[b]));
+    if (!(gmax > 0.0) || nonfinite_bits(gmax)) {
+        atomicOr(flags, (unsigned)FLAG_NONFINITE);
+        return;
+    }
+    for (int b = 0; b < nb; ++b) {
+        const double m = per_block ? __longlong_as_double((long long)bmax[b]) : gmax;
+        blocks[b].dt = cfl[0] / m;
+    }
+    time_acc[0] += cfl[0] / gmax;
+}
+
+// Sum over nodes of R^2 per conservative variable, R = -J (A - Aref),
+// warp-reduced then accumulated in FP64.
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+k_residual(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const R* __restrict__ A,
+           const float* __restrict__ Aref, const double* __restrict__ met, long long fs, double* sums) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        double r2[5] = {0, 0, 0, 0, 0};
+        if (ok) {
+            const long long e = node_index(blocks[br.b], i, j, k);
+            const double J = met[9 * fs + e];
+            for (int c = 0; c < 5; ++c) {
+                const R a = Aref ? A[c * fs + e] - (R)Aref[c * fs + e] : A[c * fs + e];
+                const double r = -J * (double)a;
+                r2[c] = r * r;
+            }
+        }
+        for (int c = 0; c < 5; ++c) {
+            double v = r2[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&sums[c], v);
+        }
+    }
+}
+
 }  // namespace
 
 // ====================================================================== launchers
+
+cudaError_t launch_setdt(DevBlock* blocks, int nb, const unsigned long long* bmax, const double* cfl, int per_block,
+                         double* time_acc, unsigned* flags, cudaStream_t s) {
+    k_setdt<<<1, 32, 0, s>>>(blocks, nb, bmax, cfl, per_block, time_acc, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Brick* bricks, int nb, const DevBlock* blocks, const void* A, const float* Aref,
+                            bool fp64, const double* met, long long fs, double* sums, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    const int g = grid_for((long long)nb * kThreads);
+    if (fp64)
+        k_residual<double><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const double*)A, nullptr, met, fs, sums);
+    else
+        k_residual<float><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)A, Aref, met, fs, sums);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_unpack(const double* src, void* dst, bool fp64, long long fs, DevBlock B, int nf,
                           cudaStream_t s) {

@@ -70,5 +70,11 @@ cudaError_t launch_rhs_out(DevBlock B, const void* A, const float* Aref, bool fp
 // Fills nf fields (field stride fs) with the per-field values v[0..nf) (device array).
 cudaError_t launch_fill_fields(void* p, bool fp64, long long fs, int nf, const double* v, cudaStream_t s);
 cudaError_t launch_fill(void* p, bool fp64, long long n, double v, cudaStream_t s);
+// dt = cfl / max wave speed per block (or the global minimum) into the block table.
+cudaError_t launch_setdt(DevBlock* blocks, int nb, const unsigned long long* bmax, const double* cfl, int per_block,
+                         double* time_acc, unsigned* flags, cudaStream_t s);
+// sums[c] += sum over nodes of R_c^2 (R = -J (A - Aref)).
+cudaError_t launch_residual(const Brick* bricks, int nb, const DevBlock* blocks, const void* A, const float* Aref,
+                            bool fp64, const double* met, long long fs, double* sums, cudaStream_t s);
 
 }  // namespace hx

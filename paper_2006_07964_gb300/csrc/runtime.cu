@@ -86,6 +86,8 @@ struct hx_ctx {
     bool tuned = false;
 
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec_cfl[2] = {nullptr, nullptr};   // step with on-device dt: global / per block
+    double* d_scal = nullptr;   // [0] cfl, [1] simulated-time accumulator, [2..6] residual sums
     std::vector<double> dt_dev;   // dt currently in the device block table
     int launches_per_step = 0;
 
@@ -429,6 +431,37 @@ int autotune(hx_ctx* ctx) {
     return HX_OK;
 }
 
+// One RK step whose dt comes from the state on the device: the CFL maxima
+// (k_dt), dt into the block table (k_setdt), then the three stages.
+int enqueue_cfl_step(hx_ctx* ctx, int per_block) {
+    const int nb = (int)ctx->blocks.size();
+    HX_CK(cudaMemsetAsync(ctx->d_bmax, 0, nb * sizeof(unsigned long long), ctx->stream));
+    HX_CK(launch_dt(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->Qn, ctx->met, ctx->fs, ctx->gas, ctx->d_bmax,
+                    ctx->stream));
+    HX_CK(launch_setdt(ctx->d_blocks, nb, ctx->d_bmax, ctx->d_scal, per_block, ctx->d_scal + 1, ctx->d_flags,
+                       ctx->stream));
+    return enqueue_step(ctx, nullptr);
+}
+
+int capture(hx_ctx* ctx, cudaGraphExec_t* out, int cfl_mode) {
+    cudaGraph_t g = nullptr;
+    HX_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = cfl_mode < 0 ? enqueue_step(ctx, nullptr) : enqueue_cfl_step(ctx, cfl_mode);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    return HX_OK;
+}
+
 int ensure_graph(hx_ctx* ctx) {
     if (ctx->gexec) return HX_OK;
     cudaGraph_t g = nullptr;
@@ -681,6 +714,7 @@ int hx_finalize(hx_ctx* ctx) {
     if ((rc = dalloc(ctx, (void**)&ctx->stage, (size_t)ctx->max_block_pts * 12 * 8))) return rc;
     if ((rc = dalloc(ctx, (void**)&ctx->d_flags, sizeof(unsigned)))) return rc;
     if ((rc = dalloc(ctx, (void**)&ctx->d_bmax, nb * sizeof(unsigned long long)))) return rc;
+    if ((rc = dalloc(ctx, (void**)&ctx->d_scal, 8 * sizeof(double)))) return rc;
     // state-like buffers start at a benign uniform value so that never-read
     // padding holds finite numbers
     HX_CK(launch_fill(ctx->met, true, 10 * ctx->fs, 1.0, ctx->stream));
@@ -905,6 +939,42 @@ int hx_step_multi(hx_ctx* ctx, int nsteps, const double* dt_per_block) {
     return step_common(ctx, nsteps, std::vector<double>(dt_per_block, dt_per_block + ctx->blocks.size()));
 }
 
+int hx_step_cfl(hx_ctx* ctx, int nsteps, double cfl, int per_block, double* time_advanced) {
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (nsteps < 0 || !(cfl > 0) || !std::isfinite(cfl)) return fail(ctx, HX_ERR_INVALID_ARG, "bad nsteps or cfl");
+    per_block = per_block ? 1 : 0;
+    if ((rc = autotune(ctx))) return rc;
+    if (!ctx->gexec_cfl[per_block] && (rc = capture(ctx, &ctx->gexec_cfl[per_block], per_block))) return rc;
+    const double init[2] = {cfl, 0.0};
+    HX_CK(cudaMemcpyAsync(ctx->d_scal, init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+    HX_CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned), ctx->stream));
+    for (int i = 0; i < nsteps; ++i) HX_CK(cudaGraphLaunch(ctx->gexec_cfl[per_block], ctx->stream));
+    double t = 0.0;
+    HX_CK(cudaMemcpyAsync(&t, ctx->d_scal + 1, sizeof t, cudaMemcpyDeviceToHost, ctx->stream));
+    rc = read_flags(ctx);
+    ctx->dt_dev.assign(ctx->blocks.size(), -1.0);   // the table now holds device-chosen dt
+    if (time_advanced) *time_advanced = t;
+    return rc;
+}
+
+int hx_residual(hx_ctx* ctx, double* rms) {
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (!rms) return fail(ctx, HX_ERR_INVALID_ARG, "null output");
+    if ((rc = autotune(ctx))) return rc;
+    if ((rc = enqueue_rhs(ctx, 0, nullptr, nullptr))) return rc;
+    HX_CK(cudaMemsetAsync(ctx->d_scal + 2, 0, 5 * sizeof(double), ctx->stream));
+    HX_CK(launch_residual(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->A, ctx->Aref, ctx->fp64(), ctx->met, ctx->fs,
+                          ctx->d_scal + 2, ctx->stream));
+    double sums[5];
+    HX_CK(cudaMemcpyAsync(sums, ctx->d_scal + 2, sizeof sums, cudaMemcpyDeviceToHost, ctx->stream));
+    HX_CK(cudaStreamSynchronize(ctx->stream));
+    const double n = (double)hx_points(ctx);
+    for (int c = 0; c < 5; ++c) rms[c] = std::sqrt(sums[c] / n);
+    return HX_OK;
+}
+
 int hx_rhs(hx_ctx* ctx, int block, double* r_out, int on_device) {
     int rc = check_ready(ctx);
     if (rc) return rc;
@@ -992,6 +1062,8 @@ void hx_destroy(hx_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    for (auto& g : ctx->gexec_cfl)
+        if (g) cudaGraphExecDestroy(g);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;

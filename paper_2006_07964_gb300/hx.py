@@ -30,7 +30,7 @@ EXPORTS = (
     "hx_config_default", "hx_create", "hx_add_block", "hx_set_face", "hx_finalize", "hx_compute_metrics",
     "hx_set_state", "hx_get_state", "hx_get_metrics", "hx_compute_dt", "hx_step", "hx_step_multi", "hx_rhs",
     "hx_get_gradients", "hx_profile_step", "hx_launches_per_step", "hx_points", "hx_device_bytes",
-    "hx_last_error", "hx_destroy", "hx_euler_rhs_periodic_noalloc", "hx_tuning",
+    "hx_last_error", "hx_destroy", "hx_euler_rhs_periodic_noalloc", "hx_tuning", "hx_step_cfl", "hx_residual",
 )
 
 
@@ -91,6 +91,8 @@ def load(path=None):
         "hx_destroy": (None, [CTX]),
         "hx_euler_rhs_periodic_noalloc": (I, [I, I, I, D, VP, VP, VP, VP]),
         "hx_tuning": (I, [CTX, ctypes.POINTER(I), ctypes.POINTER(I), P]),
+        "hx_step_cfl": (I, [CTX, I, D, I, P]),
+        "hx_residual": (I, [CTX, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -225,6 +227,19 @@ class Context:
             if d.shape != (len(self.dims),):
                 raise ValueError("one dt per block")
             self._check(self._lib.hx_step_multi(self._h, int(nsteps), _dp(d)))
+
+    def step_cfl(self, nsteps, cfl, per_block=False):
+        """nsteps RK3 steps with dt chosen on the device each step; returns
+        the simulated time advanced (sum of the global dt)."""
+        t = ctypes.c_double()
+        self._check(self._lib.hx_step_cfl(self._h, int(nsteps), float(cfl), int(bool(per_block)), ctypes.byref(t)))
+        return t.value
+
+    def residual(self):
+        """RMS of R over all nodes, per conservative variable (5 values)."""
+        out = np.empty(5)
+        self._check(self._lib.hx_residual(self._h, _dp(out)))
+        return out
 
     def profile_step(self, nsteps, dt):
         out = (hx_kernel_stat * 16)()

@@ -17,6 +17,9 @@ Workloads (sizes as the benchmark configurations state them):
               20), Ma 0.2, Re 3900, wall + far field, spanwise periodic
   batch       64 independent vortex instances with edge lengths drawn from
               {24, 32, 48, 64, 96} per axis (numpy default_rng(2006_07964))
+  shocktube   two Sod shock tubes back to back in a periodic box (the high
+              state in the middle half along x), Euler; exercises the
+              nonlinear WENO weights and the flux splitting at shocks
 """
 from dataclasses import dataclass, field
 import math
@@ -355,3 +358,23 @@ def batch(count=64, seed=2006_07964, edges=BATCH_EDGES, amp=0.1, steps=10):
         blocks.append(Block(xyz, periodic_faces((L, L, L), self_index=b), q))
     return Workload("batch%d" % count, blocks, gamma=g, mach=0.5, viscous=False, cfl=0.5, steps=steps,
                     meta={"dims": dims.tolist(), "seed": seed})
+
+
+def shocktube(n=(256, 8, 8), length=2.0, amp=0.0, steps=20, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1)):
+    """Periodic box [0, length) x [0, length n_j/n_i) x [0, length n_k/n_i):
+    state `left` (rho, u, p) for x in [length/4, 3 length/4), `right`
+    elsewhere (Sod's states by default), so that two Riemann problems evolve
+    from x = length/4 and x = 3 length/4 until their waves meet.  amp > 0
+    warps the grid as warped_box does (the discontinuity stays a plane in
+    physical space)."""
+    ni, nj, nk = n
+    L = (length, length * nj / ni, length * nk / ni)
+    xyz = warped_box(n, L, amp) if amp > 0 else np.stack(lattice(n, L))
+    g = 1.4
+    inside = (xyz[0] >= 0.25 * length) & (xyz[0] < 0.75 * length)
+    rho = np.where(inside, left[0], right[0])
+    u = np.where(inside, left[1], right[1])
+    p = np.where(inside, left[2], right[2])
+    q = conservative(g, rho, u, 0.0, 0.0, p)
+    return Workload("shocktube%d" % ni, [Block(xyz, periodic_faces(L), q)], gamma=g, mach=0.0, viscous=False,
+                    cfl=0.5, steps=steps, meta={"L": L, "left": left, "right": right})

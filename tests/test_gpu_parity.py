@@ -78,6 +78,7 @@ CASES = {
     "split_ns": lambda: split(warped((30, 24, 20), viscous=True, reynolds=100.0), (2, 2, 1)),
     "ogrid_s4": lambda: W.ogrid(scale=4),
     "ogrid_s8": lambda: W.ogrid(scale=8),
+    "shock_warped": lambda: W.shocktube((96, 12, 12), amp=0.04),
 }
 
 
@@ -132,7 +133,7 @@ def test_free_stream_residual_gpu():
 # ---------------------------------------------------------------- steps
 
 @pytest.mark.parametrize("name,steps", [("vortex32", 10), ("ragged_euler", 4), ("tgv24", 5), ("split_ns", 3),
-                                        ("ogrid_s4", 5)])
+                                        ("ogrid_s4", 5), ("shock_warped", 20)])
 def test_steps_parity(name, steps):
     w, ctx, P = pair(name)
     dt, _ = P.dt(0.5)
@@ -322,3 +323,43 @@ def test_error_invalid_args():
         ctx.add_block(np.zeros((3, 4, 4, 4)))
     with pytest.raises(hx.HxError):
         ctx.finalize()
+
+
+# ---------------------------------------------------------------- device-chosen dt, residual norm
+
+@pytest.mark.parametrize("name", ["vortex32", "ogrid_s8"])
+def test_step_with_device_cfl_matches_oracle(name):
+    """Each step's dt is reduced on the device from the state; the oracle
+    recomputes dt from its own state before every step."""
+    w, ctx, P = pair(name)
+    t_gpu = ctx.step_cfl(3, 0.5)
+    t_orc = 0.0
+    for _ in range(3):
+        dt, _ = P.dt(0.5)
+        P.step(1, dt)
+        t_orc += dt
+    assert t_gpu == pytest.approx(t_orc, rel=1e-12)
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.get_state(b), P.get_state(b)) < TOL
+
+
+def test_step_with_device_cfl_per_block():
+    w = W.batch(count=4, seed=11)
+    ctx = hx.from_workload(w)
+    P = oracle.from_workload(w)
+    ctx.step_cfl(2, 0.5, per_block=True)
+    for _ in range(2):
+        _, per = P.dt(0.5)
+        P.step(1, per)
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.get_state(b), P.get_state(b)) < TOL
+
+
+@pytest.mark.parametrize("name", ["tgv24", "split_ns"])
+def test_residual_norm_matches_oracle(name):
+    w, ctx, P = pair(name)
+    P.rhs()
+    n = sum(b.npts for b in w.blocks)
+    want = np.sqrt(sum((P.get_rhs(b) ** 2).reshape(5, -1).sum(axis=1) for b in range(len(w.blocks))) / n)
+    got = ctx.residual()
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-12 * want.max())

@@ -2,7 +2,8 @@
 invariants: exact metrics on affine grids, periodic metrics, free-stream
 preservation, discrete conservation, multi-block = single block, the
 isentropic vortex's convergence order, RK3's temporal order, viscous decay
-rates and the TGV dissipation rate."""
+rates, the TGV dissipation rate and the exact Riemann solution of Sod's
+shock tube."""
 import numpy as np
 import pytest
 
@@ -315,3 +316,35 @@ def test_tgv_viscous_dissipation_rate():
     dK = ((u * dR[1] + v * dR[2] + ww * dR[3] - 0.5 * (u * u + v * v + ww * ww) * dR[0]) / J).sum()
     nu = w.mach / w.reynolds
     assert -dK / K == pytest.approx(6 * nu, rel=0.02)
+
+
+# ---------------------------------------------------------------- shocks (exact Riemann solution)
+
+def _sod_l1(n, T=0.2):
+    import riemann_exact as RE
+    w = W.shocktube((n, 6, 6))
+    P = oracle.from_workload(w)
+    t = 0.0
+    while t < T - 1e-12:
+        dt, _ = P.dt(0.5)
+        dt = min(dt, T - t)
+        P.step(1, dt)
+        t += dt
+    rho = P.get_state(0)[0][0, 0]
+    x = w.blocks[0].xyz[0][0, 0]
+    xi = np.where(x >= 1.0, (x - 1.5) / T, (0.5 - x) / T)   # the two tubes, mirror images
+    ex = RE.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), G, xi)
+    return np.abs(rho - ex[0]).mean(), rho
+
+
+def test_sod_shock_tube_against_exact_riemann_solution():
+    """Two Sod problems in a periodic box at t = 0.2: density within L1 7.5e-3
+    of the exact Riemann solution at 200 nodes, first-order convergence under
+    refinement (discontinuities), no overshoot beyond 1e-3 (non-oscillatory
+    characteristic WENO with Steger-Warming splitting)."""
+    e1, rho1 = _sod_l1(200)
+    e2, rho2 = _sod_l1(400)
+    assert e1 < 7.5e-3
+    assert 0.7 < np.log2(e1 / e2) < 1.3
+    for rho in (rho1, rho2):
+        assert rho.max() < 1.0 + 1e-3 and rho.min() > 0.125 - 1e-3
