@@ -308,6 +308,45 @@ def batch_report(torch, hx, w, steps, warmup, stream):
     return out
 
 
+def scheme_report(torch, hx, w, steps, warmup, stream):
+    """The paper's modified AFWENO (characteristic space at the node,
+    indicators shared) against its original AFWENO (characteristic space at
+    the face, two WENOs per face): throughput of both on the workload in
+    both forms, and accuracy on the 32^3 warped isentropic vortex after 10
+    steps against the exact translated vortex."""
+    from paper_2006_07964_gb300 import workloads as W
+    out = {"report": "scheme", "workload": w.name, "points": w.npts, "steps": steps}
+    probe = hx.from_workload(w, precision="fp64", stream=stream.cuda_stream)
+    dt, _ = probe.compute_dt(0.5)
+    probe.close()
+    for scheme, name in ((0, "modified"), (1, "original")):
+        for form in ("fp64", "mixed"):
+            ctx = hx.from_workload(w, precision=form, stream=stream.cuda_stream, scheme=scheme)
+            ctx.step(warmup, dt)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.step(steps, dt)
+            e1.record(stream)
+            e1.synchronize()
+            secs = e0.elapsed_time(e1) / 1e3
+            out["%s_%s_mpts" % (name, form)] = w.npts * 3 * steps / secs / 1e6
+            ctx.close()
+        v = W.vortex(32)
+        ctx = hx.from_workload(v, precision="fp64", stream=stream.cuda_stream, scheme=scheme)
+        vdt, _ = ctx.compute_dt(0.5)
+        ctx.step(10, vdt)
+        xyz = v.blocks[0].xyz
+        ex = W.conservative(v.gamma, *W.isentropic_vortex(v.gamma, xyz[0], xyz[1], t=10 * vdt))
+        q = ctx.get_state(0)
+        out["%s_vortex32_rms_error" % name] = float(np.sqrt(((q - ex) ** 2).mean()))
+        out["%s_vortex32_max_error" % name] = float(np.abs(q - ex).max())
+        ctx.close()
+    for form in ("fp64", "mixed"):
+        out["speedup_modified_vs_original_" + form] = out["modified_%s_mpts" % form] / out["original_%s_mpts" % form]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,7 +357,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--forms", default="fp64,mixed", help="comma list of fp64, mixed")
-    ap.add_argument("--report", choices=["precision", "batch"], default=None,
+    ap.add_argument("--report", choices=["precision", "batch", "scheme"], default=None,
                     help="print a precision (mixed vs FP64 errors) or batch (batched vs per-instance) report "
                          "instead of the benchmark line")
     args = ap.parse_args()
@@ -375,6 +414,9 @@ def main():
         return
     if args.report == "batch":
         print(json.dumps(batch_report(torch, hx, w, args.steps, args.warmup, stream)))
+        return
+    if args.report == "scheme":
+        print(json.dumps(scheme_report(torch, hx, w, args.steps, args.warmup, stream)))
         return
 
     ranks = Ranks(world)

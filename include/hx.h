@@ -76,7 +76,10 @@ typedef struct {
     double sutherland_s;  /* S of Sutherland's law (110.4/288.15)                       */
     int precision;        /* HX_FP64, or HX_MIXED: FP32 state, fluxes and WENO with FP32
                              accumulation; FP64 metrics, Jacobian and RK combination    */
-    int scheme;           /* 0: modified AFWENO (the only scheme built)                 */
+    int scheme;           /* 0: modified AFWENO (characteristic space at the node, shared
+                             indicators, Figs. 10-11); 1: the original AFWENO
+                             (characteristic space at the face, two WENOs per face,
+                             Fig. 9), kept to measure the modification              */
     size_t mem_cap_bytes; /* 0: no cap; else hx_finalize fails with HX_ERR_OOM above it */
     int autotune;         /* 1: time the tile-shape candidates once per shape class     */
 } hx_config;

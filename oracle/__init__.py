@@ -112,9 +112,9 @@ class Problem:
     """
 
     def __init__(self, gamma=1.4, mach=0.5, reynolds=1.0, prandtl=0.72,
-                 sutherland_s=110.4 / 288.15, viscous=False, mu_law=1):
+                 sutherland_s=110.4 / 288.15, viscous=False, mu_law=1, scheme=0):
         self._lib = load()
-        cfg = np.array([gamma, mach, reynolds, prandtl, sutherland_s, float(viscous), float(mu_law)])
+        cfg = np.array([gamma, mach, reynolds, prandtl, sutherland_s, float(viscous), float(mu_law), float(scheme)])
         self._h = self._lib.orc_new(_p(cfg))
         self.gamma = gamma
         self.dims = []
@@ -193,11 +193,12 @@ class Problem:
         return g, per
 
 
-def from_workload(w):
+def from_workload(w, scheme=0):
     """Builds an oracle Problem from a workload description (blocks, faces,
-    initial state) produced by ``paper_2006_07964_gb300.workloads``."""
+    initial state) produced by ``paper_2006_07964_gb300.workloads``;
+    scheme 0 is the modified AFWENO, 1 the original one."""
     P = Problem(gamma=w.gamma, mach=w.mach, reynolds=w.reynolds, prandtl=w.prandtl,
-                sutherland_s=w.sutherland_s, viscous=w.viscous, mu_law=w.mu_law)
+                sutherland_s=w.sutherland_s, viscous=w.viscous, mu_law=w.mu_law, scheme=scheme)
     for blk in w.blocks:
         P.add_block(blk.xyz)
     for b, blk in enumerate(w.blocks):

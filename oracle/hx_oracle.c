@@ -57,6 +57,11 @@
  *       tangential velocity upwinded by the sign of the normal velocity.
  *   R11 viscosity: mu = 1 or Sutherland T^(3/2)(1+S)/(T+S).
  *   R12 tau and q carry the factor Ma/Re; q = Ma mu/(Re Pr (gamma-1)) dT/dx_j.
+ *   R13 original AFWENO (Fig. 9): the characteristic space of face i+1/2 is
+ *       built from the arithmetic mean of Q_i and Q_{i+1} and the unit normal
+ *       of the face metric; the left-biased value comes from the nodes
+ *       i-2..i+2 and the right-biased one from i-1..i+3, each with its own
+ *       smoothness indicators.
  * Parity of the physical-face rules (R9, R10) is unpinned: the paper gives no
  * formulas for them.
  */
@@ -89,6 +94,7 @@ typedef struct {
 typedef struct {
     double gamma, mach, re, pr, suth;
     int viscous, mu_law;
+    int scheme;     /* 0: modified AFWENO (Figs. 10-11), 1: original AFWENO (Fig. 9) */
     int nb, cap;
     oblock *b;
 } oproblem;
@@ -574,35 +580,74 @@ static void inviscid_line(const oproblem *P, double *const *Qs, int b, int d, co
         point_flux(P, q, m, f);
         for (int c = 0; c < 5; ++c) Fp[c * L + p + O] = f[c];
     }
-    /* characteristic-space WENO at node p: U^L_{p+1/2} and U^R_{p-1/2} */
-    for (int p = -1; p <= n; ++p) {
-        double q[5], m[3], k[3], Le[25], Re[25], lam[5];
-        for (int c = 0; c < 5; ++c) q[c] = Q[c * L + p + O];
-        for (int c = 0; c < 3; ++c) m[c] = mc[c][p + O];
-        const double mm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-        for (int c = 0; c < 3; ++c) k[c] = m[c] / mm;
-        eigen(P, q, k, Le, Re, lam);
-        double WL[5], WR[5];
-        for (int l = 0; l < 5; ++l) {
-            double W[5];
-            for (int s = -2; s <= 2; ++s) {
-                double acc = 0.0;
-                for (int c = 0; c < 5; ++c) acc += Le[l * 5 + c] * Q[c * L + p + s + O];
-                W[s + 2] = acc;
-            }
-            double bt[3];
-            weno_beta(W, bt);
-            WL[l] = weno_left(W, bt);
-            WR[l] = weno_right(W, bt);
-        }
-        for (int c = 0; c < 5; ++c) {
-            double al = 0.0, ar = 0.0;
+    if (P->scheme == 0) {
+        /* modified AFWENO: characteristic space at node p gives
+         * U^L_{p+1/2} and U^R_{p-1/2} from one stencil and shared indicators */
+        for (int p = -1; p <= n; ++p) {
+            double q[5], m[3], k[3], Le[25], Re[25], lam[5];
+            for (int c = 0; c < 5; ++c) q[c] = Q[c * L + p + O];
+            for (int c = 0; c < 3; ++c) m[c] = mc[c][p + O];
+            const double mm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            for (int c = 0; c < 3; ++c) k[c] = m[c] / mm;
+            eigen(P, q, k, Le, Re, lam);
+            double WL[5], WR[5];
             for (int l = 0; l < 5; ++l) {
-                al += Re[c * 5 + l] * WL[l];
-                ar += Re[c * 5 + l] * WR[l];
+                double W[5];
+                for (int s = -2; s <= 2; ++s) {
+                    double acc = 0.0;
+                    for (int c = 0; c < 5; ++c) acc += Le[l * 5 + c] * Q[c * L + p + s + O];
+                    W[s + 2] = acc;
+                }
+                double bt[3];
+                weno_beta(W, bt);
+                WL[l] = weno_left(W, bt);
+                WR[l] = weno_right(W, bt);
             }
-            UL[c * L + p + O] = al;
-            UR[c * L + p + O] = ar;
+            for (int c = 0; c < 5; ++c) {
+                double al = 0.0, ar = 0.0;
+                for (int l = 0; l < 5; ++l) {
+                    al += Re[c * 5 + l] * WL[l];
+                    ar += Re[c * 5 + l] * WR[l];
+                }
+                UL[c * L + p + O] = al;
+                UR[c * L + p + O] = ar;
+            }
+        }
+    } else {
+        /* original AFWENO (Fig. 9, reading R13): characteristic space at face
+         * f+1/2 from the mean state and the face metric; two independent
+         * WENO interpolations per face.  U^L of face f is kept at UL[f],
+         * U^R of face f at UR[f+1], as in the modified scheme. */
+        for (int f = -1; f <= n - 1; ++f) {
+            double q[5], mf[3], k[3], Le[25], Re[25], lam[5];
+            for (int c = 0; c < 5; ++c) q[c] = 0.5 * (Q[c * L + f + O] + Q[c * L + f + 1 + O]);
+            for (int c = 0; c < 3; ++c) mf[c] = mid6(mc[c] + f + O);
+            const double mm = sqrt(mf[0] * mf[0] + mf[1] * mf[1] + mf[2] * mf[2]);
+            for (int c = 0; c < 3; ++c) k[c] = mf[c] / mm;
+            eigen(P, q, k, Le, Re, lam);
+            double WL[5], WR[5];
+            for (int l = 0; l < 5; ++l) {
+                double W[6];
+                for (int s = -2; s <= 3; ++s) {
+                    double acc = 0.0;
+                    for (int c = 0; c < 5; ++c) acc += Le[l * 5 + c] * Q[c * L + f + s + O];
+                    W[s + 2] = acc;
+                }
+                double bl[3], br[3];
+                weno_beta(W, bl);       /* stencil f-2..f+2 */
+                weno_beta(W + 1, br);   /* stencil f-1..f+3 */
+                WL[l] = weno_left(W, bl);
+                WR[l] = weno_right(W + 1, br);
+            }
+            for (int c = 0; c < 5; ++c) {
+                double al = 0.0, ar = 0.0;
+                for (int l = 0; l < 5; ++l) {
+                    al += Re[c * 5 + l] * WL[l];
+                    ar += Re[c * 5 + l] * WR[l];
+                }
+                UL[c * L + f + O] = al;
+                UR[c * L + f + 1 + O] = ar;
+            }
         }
     }
     /* Steger-Warming numerical flux at faces f+1/2, f = -1..n-1 */
@@ -814,7 +859,7 @@ static void bc_nodes(oproblem *P, double *const *Qs) {
 /* exported API (ctypes)                                                     */
 /* ------------------------------------------------------------------------ */
 
-/* cfg = {gamma, mach, reynolds, prandtl, sutherland_s, viscous, mu_law} */
+/* cfg = {gamma, mach, reynolds, prandtl, sutherland_s, viscous, mu_law, scheme} */
 void *orc_new(const double *cfg) {
     oproblem *P = (oproblem *)calloc(1, sizeof(oproblem));
     P->gamma = cfg[0];
@@ -824,6 +869,7 @@ void *orc_new(const double *cfg) {
     P->suth = cfg[4];
     P->viscous = (int)cfg[5];
     P->mu_law = (int)cfg[6];
+    P->scheme = (int)cfg[7];
     return P;
 }
 

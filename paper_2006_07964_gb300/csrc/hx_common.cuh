@@ -244,6 +244,37 @@ __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3
     right = __fdividef(tR1 * uR1 + tR2 * uR2 + tR3 * uR3, tR1 + tR2 + tR3);
 }
 
+// One WENO5 value with its own indicators (original AFWENO, Fig. 9): the
+// left-biased value at i+1/2 (LEFT) or the right-biased value at i-1/2 of
+// the stencil W[-2..2] of node i.
+template <class R, bool LEFT>
+__device__ __forceinline__ R weno_one(R w0, R w1, R w2, R w3, R w4) {
+    const R eps = R(1.0e-6);
+    const R a1 = w0 - R(2) * w1 + w2, c1 = w0 - R(4) * w1 + R(3) * w2;
+    const R a2 = w1 - R(2) * w2 + w3, c2 = w1 - w3;
+    const R a3 = w2 - R(2) * w3 + w4, c3 = R(3) * w2 - R(4) * w3 + w4;
+    R s1 = eps + R(13.0 / 12.0) * a1 * a1 + R(0.25) * c1 * c1;
+    R s2 = eps + R(13.0 / 12.0) * a2 * a2 + R(0.25) * c2 * c2;
+    R s3 = eps + R(13.0 / 12.0) * a3 * a3 + R(0.25) * c3 * c3;
+    s1 *= s1;
+    s2 *= s2;
+    s3 *= s3;
+    const R p12 = s1 * s2, p13 = s1 * s3, p23 = s2 * s3;
+    if (LEFT) {
+        const R u1 = R(0.375) * w0 - R(1.25) * w1 + R(1.875) * w2;
+        const R u2 = R(-0.125) * w1 + R(0.75) * w2 + R(0.375) * w3;
+        const R u3 = R(0.375) * w2 + R(0.75) * w3 - R(0.125) * w4;
+        const R t1 = R(0.0625) * p23, t2 = R(0.625) * p13, t3 = R(0.3125) * p12;
+        return (t1 * u1 + t2 * u2 + t3 * u3) / (t1 + t2 + t3);
+    } else {
+        const R u1 = R(0.375) * w4 - R(1.25) * w3 + R(1.875) * w2;
+        const R u2 = R(-0.125) * w3 + R(0.75) * w2 + R(0.375) * w1;
+        const R u3 = R(0.375) * w2 + R(0.75) * w1 - R(0.125) * w0;
+        const R t1 = R(0.0625) * p12, t2 = R(0.625) * p13, t3 = R(0.3125) * p23;
+        return (t1 * u1 + t2 * u2 + t3 * u3) / (t1 + t2 + t3);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Characteristic basis at a node: Pulliam-Chaussee eigenvectors of the
 // Jacobian of k.F for the unit normal k of the node metric.  The projection

@@ -55,7 +55,10 @@ struct FluxLayout {
 // RK (last sweep only): instead of storing A, finish R = -J (A + div) and
 // the RK3 stage combination at each output node (Eq. (20), FP64), with the
 // wall-node values and the non-finite / non-physical flags.
-template <class R, int DIR, int TP, int NA, bool VISC, bool RK>
+// SCH 0: modified AFWENO (characteristic space at the node, Figs. 10-11);
+// SCH 1: original AFWENO (characteristic space at the face from the mean
+// state and the face metric, two independent WENOs per face, Fig. 9).
+template <class R, int DIR, int TP, int NA, bool VISC, bool RK, int SCH>
 __global__ void __launch_bounds__(TP * NA)
 k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int ntiles,
        const R* __restrict__ Q, const R* __restrict__ met, long long fs, const R* __restrict__ stress,
@@ -139,7 +142,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         sFv[2 * PL + s0] = mx * S[4] + my * S[5] + mz * S[2];
                         sFv[3 * PL + s0] = mx * S[6] + my * S[7] + mz * S[8];
                     }
-                    if (p < -1 || p > n) continue;   // WENO only where a face needs it
+                    if (SCH == 1 || p < -1 || p > n) continue;   // WENO only where a face needs it
                     R W[5][5];
 #pragma unroll
                     for (int s = -2; s <= 2; ++s) {
@@ -180,10 +183,33 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     const R kx = mf[0] * imm, ky = mf[1] * imm, kz = mf[2] * imm;
                     const int uf = LY::idx(f, a), ur = LY::idx(f + 1, a);
                     R ql[5], qr[5], Fp[5], Fm[5];
+                    if (SCH == 0) {
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        ql[k] = sUL[k * PL + uf];
-                        qr[k] = sUR[k * PL + ur];
+                        for (int k = 0; k < 5; ++k) {
+                            ql[k] = sUL[k * PL + uf];
+                            qr[k] = sUR[k * PL + ur];
+                        }
+                    } else {
+                        R qm[5];
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) qm[k] = R(0.5) * (sQ[k * PL + uf] + sQ[k * PL + ur]);
+                        CharBasis<R> cb;
+                        cb.init(gs, qm, mf[0], mf[1], mf[2]);
+                        R W[6][5];
+#pragma unroll
+                        for (int s = -2; s <= 3; ++s) {
+                            const int si = LY::idx(f + s, a);
+                            cb.project(sQ[si], sQ[PL + si], sQ[2 * PL + si], sQ[3 * PL + si], sQ[4 * PL + si],
+                                       W[s + 2]);
+                        }
+                        R WL[5], WR[5];
+#pragma unroll
+                        for (int l = 0; l < 5; ++l) {
+                            WL[l] = weno_one<R, true>(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l]);
+                            WR[l] = weno_one<R, false>(W[1][l], W[2][l], W[3][l], W[4][l], W[5][l]);
+                        }
+                        cb.back(WL, ql);
+                        cb.back(WR, qr);
                     }
                     sw_flux<R, true>(gs, ql, kx, ky, kz, mm, Fp);
                     sw_flux<R, false>(gs, qr, kx, ky, kz, mm, Fm);

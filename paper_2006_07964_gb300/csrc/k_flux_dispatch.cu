@@ -5,12 +5,12 @@
 
 namespace hx {
 
-int flux_ctas_f64_d0(int, bool, bool);
-int flux_ctas_f64_d1(int, bool, bool);
-int flux_ctas_f64_d2(int, bool, bool);
-int flux_ctas_f32_d0(int, bool, bool);
-int flux_ctas_f32_d1(int, bool, bool);
-int flux_ctas_f32_d2(int, bool, bool);
+int flux_ctas_f64_d0(int, bool, bool, int);
+int flux_ctas_f64_d1(int, bool, bool, int);
+int flux_ctas_f64_d2(int, bool, bool, int);
+int flux_ctas_f32_d0(int, bool, bool, int);
+int flux_ctas_f32_d1(int, bool, bool, int);
+int flux_ctas_f32_d2(int, bool, bool, int);
 cudaError_t flux_run_f64_d0(int, bool, const FluxArgs&, cudaStream_t);
 cudaError_t flux_run_f64_d1(int, bool, const FluxArgs&, cudaStream_t);
 cudaError_t flux_run_f64_d2(int, bool, const FluxArgs&, cudaStream_t);
@@ -30,12 +30,12 @@ size_t flux_smem(bool fp64, int dir, int v, bool visc) {
     return (fp64 ? 8 : 4) * plane * (visc ? 27 : 23);
 }
 
-int flux_ctas_per_sm(bool fp64, int dir, int v, bool visc, bool rk) {
+int flux_ctas_per_sm(bool fp64, int dir, int v, bool visc, bool rk, int scheme) {
     if (fp64)
-        return dir == 0 ? flux_ctas_f64_d0(v, visc, rk) : dir == 1 ? flux_ctas_f64_d1(v, visc, rk)
-                                                                 : flux_ctas_f64_d2(v, visc, rk);
-    return dir == 0 ? flux_ctas_f32_d0(v, visc, rk) : dir == 1 ? flux_ctas_f32_d1(v, visc, rk)
-                                                             : flux_ctas_f32_d2(v, visc, rk);
+        return dir == 0 ? flux_ctas_f64_d0(v, visc, rk, scheme) : dir == 1 ? flux_ctas_f64_d1(v, visc, rk, scheme)
+                                                                         : flux_ctas_f64_d2(v, visc, rk, scheme);
+    return dir == 0 ? flux_ctas_f32_d0(v, visc, rk, scheme) : dir == 1 ? flux_ctas_f32_d1(v, visc, rk, scheme)
+                                                                     : flux_ctas_f32_d2(v, visc, rk, scheme);
 }
 
 cudaError_t launch_flux(bool fp64, int dir, int v, bool visc, const FluxArgs& a, cudaStream_t s) {

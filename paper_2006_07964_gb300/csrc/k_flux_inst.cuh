@@ -16,13 +16,13 @@ constexpr int flux_na(int dir, int v) { return dir == 0 ? (v == 0 ? 8 : v == 1 ?
 
 namespace {
 
-template <class R, int DIR, int V, bool VISC, bool RK = false>
+template <class R, int DIR, int V, bool VISC, bool RK = false, int SCH = 0>
 struct FluxInst {
     static constexpr int TP = flux_tp(DIR, V), NA = flux_na(DIR, V);
     static constexpr size_t smem = FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC>();
     static int ctas() {
-        cudaFuncSetAttribute(k_flux<R, DIR, TP, NA, VISC, RK>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        auto kern = k_flux<R, DIR, TP, NA, VISC, RK>;
+        cudaFuncSetAttribute(k_flux<R, DIR, TP, NA, VISC, RK, SCH>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        auto kern = k_flux<R, DIR, TP, NA, VISC, RK, SCH>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
             cudaGetLastError();
             return 0;
@@ -37,7 +37,7 @@ struct FluxInst {
     static cudaError_t run(const FluxArgs& a, cudaStream_t s) {
         GasR<R> gs;
         gs.init(a.gas);
-        k_flux<R, DIR, TP, NA, VISC, RK><<<a.grid, TP * NA, smem, s>>>(
+        k_flux<R, DIR, TP, NA, VISC, RK, SCH><<<a.grid, TP * NA, smem, s>>>(
             a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, a.fs, (const R*)a.stress, (R*)a.A,
             a.accumulate, gs, a.rk);
         return cudaGetLastError();
@@ -46,54 +46,42 @@ struct FluxInst {
 
 }  // namespace
 
-int HX_CAT3(flux_ctas_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc, bool rk) {
+namespace {
+
+template <int SCH, class F>
+auto pick(int v, bool visc, bool rk, F&& f) {
     using R = HX_FLUX_R;
     constexpr int D = HX_FLUX_DIR;
-    if (rk && D == 2) {
-        switch (v * 2 + (visc ? 1 : 0)) {
-            case 0: return FluxInst<R, D, 0, false, D == 2>::ctas();
-            case 1: return FluxInst<R, D, 0, true, D == 2>::ctas();
-            case 2: return FluxInst<R, D, 1, false, D == 2>::ctas();
-            case 3: return FluxInst<R, D, 1, true, D == 2>::ctas();
-            case 4: return FluxInst<R, D, 2, false, D == 2>::ctas();
-            case 5: return FluxInst<R, D, 2, true, D == 2>::ctas();
-        }
-        return 0;
+    constexpr bool CanRK = D == 2;
+    const int key = v * 4 + (visc ? 2 : 0) + (rk && CanRK ? 1 : 0);
+    switch (key) {
+        case 0: return f(FluxInst<R, D, 0, false, false, SCH>{});
+        case 1: return f(FluxInst<R, D, 0, false, CanRK, SCH>{});
+        case 2: return f(FluxInst<R, D, 0, true, false, SCH>{});
+        case 3: return f(FluxInst<R, D, 0, true, CanRK, SCH>{});
+        case 4: return f(FluxInst<R, D, 1, false, false, SCH>{});
+        case 5: return f(FluxInst<R, D, 1, false, CanRK, SCH>{});
+        case 6: return f(FluxInst<R, D, 1, true, false, SCH>{});
+        case 7: return f(FluxInst<R, D, 1, true, CanRK, SCH>{});
+        case 8: return f(FluxInst<R, D, 2, false, false, SCH>{});
+        case 9: return f(FluxInst<R, D, 2, false, CanRK, SCH>{});
+        case 10: return f(FluxInst<R, D, 2, true, false, SCH>{});
+        default: return f(FluxInst<R, D, 2, true, CanRK, SCH>{});
     }
-    switch (v * 2 + (visc ? 1 : 0)) {
-        case 0: return FluxInst<R, D, 0, false>::ctas();
-        case 1: return FluxInst<R, D, 0, true>::ctas();
-        case 2: return FluxInst<R, D, 1, false>::ctas();
-        case 3: return FluxInst<R, D, 1, true>::ctas();
-        case 4: return FluxInst<R, D, 2, false>::ctas();
-        case 5: return FluxInst<R, D, 2, true>::ctas();
-    }
-    return 0;
+}
+
+}  // namespace
+
+int HX_CAT3(flux_ctas_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc, bool rk, int scheme) {
+    if (v < 0 || v > 2) return 0;
+    auto f = [](auto inst) { return decltype(inst)::ctas(); };
+    return scheme ? pick<1>(v, visc, rk, f) : pick<0>(v, visc, rk, f);
 }
 
 cudaError_t HX_CAT3(flux_run_, HX_FLUX_NAME, HX_FLUX_DIR)(int v, bool visc, const FluxArgs& a, cudaStream_t s) {
-    using R = HX_FLUX_R;
-    constexpr int D = HX_FLUX_DIR;
-    if (a.fuse_rk && D == 2) {
-        switch (v * 2 + (visc ? 1 : 0)) {
-            case 0: return FluxInst<R, D, 0, false, D == 2>::run(a, s);
-            case 1: return FluxInst<R, D, 0, true, D == 2>::run(a, s);
-            case 2: return FluxInst<R, D, 1, false, D == 2>::run(a, s);
-            case 3: return FluxInst<R, D, 1, true, D == 2>::run(a, s);
-            case 4: return FluxInst<R, D, 2, false, D == 2>::run(a, s);
-            case 5: return FluxInst<R, D, 2, true, D == 2>::run(a, s);
-        }
-        return cudaErrorInvalidValue;
-    }
-    switch (v * 2 + (visc ? 1 : 0)) {
-        case 0: return FluxInst<R, D, 0, false>::run(a, s);
-        case 1: return FluxInst<R, D, 0, true>::run(a, s);
-        case 2: return FluxInst<R, D, 1, false>::run(a, s);
-        case 3: return FluxInst<R, D, 1, true>::run(a, s);
-        case 4: return FluxInst<R, D, 2, false>::run(a, s);
-        case 5: return FluxInst<R, D, 2, true>::run(a, s);
-    }
-    return cudaErrorInvalidValue;
+    if (v < 0 || v > 2) return cudaErrorInvalidValue;
+    auto f = [&](auto inst) { return decltype(inst)::run(a, s); };
+    return a.scheme ? pick<1>(v, visc, a.fuse_rk != 0, f) : pick<0>(v, visc, a.fuse_rk != 0, f);
 }
 
 }  // namespace hx

@@ -21,6 +21,7 @@ struct FluxArgs {
     Gas gas;
     int grid;           // CTAs of the persistent launch
     int fuse_rk;        // zeta sweep only: finish R and the RK3 stage instead of storing A
+    int scheme;         // 0 modified AFWENO, 1 original AFWENO
     RKArgs rk;
 };
 
@@ -33,7 +34,7 @@ FluxShape flux_shape(int dir, int variant);
 size_t flux_smem(bool fp64, int dir, int variant, bool visc);
 // CTAs per SM the variant can keep resident (0 if it cannot launch); also
 // sets the kernel's shared-memory opt-in.
-int flux_ctas_per_sm(bool fp64, int dir, int variant, bool visc, bool rk = false);
+int flux_ctas_per_sm(bool fp64, int dir, int variant, bool visc, bool rk = false, int scheme = 0);
 cudaError_t launch_flux(bool fp64, int dir, int variant, bool visc, const FluxArgs& a, cudaStream_t s);
 
 // ---- everything else (k_misc.cu) ----------------------------------------

@@ -287,6 +287,7 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
         a.accumulate = d > 0;
         a.gas = ctx->gas;
         a.grid = ctx->grid[d];
+        a.scheme = ctx->cfg.scheme;
         const bool fuse = d == 2 && rk;
         if (fuse) {
             a.fuse_rk = 1;
@@ -361,7 +362,7 @@ int autotune(hx_ctx* ctx) {
     long long cls = 1;
     while (cls < tot) cls <<= 1;
     for (int d = 0; d < 3; ++d) {
-        auto key = std::make_tuple((int)f64, d, (int)visc, cls, nmin[d], (int)ctx->blocks.size());
+        auto key = std::make_tuple((int)f64 + 2 * ctx->cfg.scheme, d, (int)visc, cls, nmin[d], (int)ctx->blocks.size());
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune.find(key);
@@ -377,7 +378,7 @@ int autotune(hx_ctx* ctx) {
             HX_CK(cudaEventCreate(&e0));
             HX_CK(cudaEventCreate(&e1));
             for (int v = 0; v < kFluxVariants; ++v) {
-                const int cps = flux_ctas_per_sm(f64, d, v, visc);
+                const int cps = flux_ctas_per_sm(f64, d, v, visc, false, ctx->cfg.scheme);
                 if (cps <= 0) continue;
                 FluxArgs a{};
                 a.blocks = ctx->d_blocks;
@@ -390,6 +391,7 @@ int autotune(hx_ctx* ctx) {
                 a.A = ctx->A;
                 a.accumulate = 0;
                 a.gas = ctx->gas;
+                a.scheme = ctx->cfg.scheme;
                 a.grid = (int)std::min<long long>(a.ntiles, (long long)cps * ctx->num_sms);
                 HX_CK(launch_flux(f64, d, v, visc, a, ctx->stream));   // warm-up
                 HX_CK(cudaEventRecord(e0, ctx->stream));
@@ -409,7 +411,7 @@ int autotune(hx_ctx* ctx) {
             cudaEventDestroy(e1);
         } else {
             for (int v = 0; v < kFluxVariants && best < 0; ++v)
-                if (flux_ctas_per_sm(f64, d, v, visc) > 0) best = v;
+                if (flux_ctas_per_sm(f64, d, v, visc, false, ctx->cfg.scheme) > 0) best = v;
         }
         if (best < 0) return fail(ctx, HX_ERR_CUDA, "no flux kernel variant can launch on this device");
         ctx->variant[d] = best;
@@ -417,12 +419,12 @@ int autotune(hx_ctx* ctx) {
         g_tune[key] = best;
     }
     for (int d = 0; d < 3; ++d) {
-        const int cps = std::max(1, flux_ctas_per_sm(f64, d, ctx->variant[d], visc));
+        const int cps = std::max(1, flux_ctas_per_sm(f64, d, ctx->variant[d], visc, false, ctx->cfg.scheme));
         ctx->grid[d] = (int)std::max<long long>(
             1, std::min<long long>(ctx->ntiles[d][ctx->variant[d]], (long long)cps * ctx->num_sms));
     }
     {   // the zeta sweep with the fused RK stage (attributes set here, before any capture)
-        const int cps = flux_ctas_per_sm(f64, 2, ctx->variant[2], visc, true);
+        const int cps = flux_ctas_per_sm(f64, 2, ctx->variant[2], visc, true, ctx->cfg.scheme);
         if (cps <= 0) return fail(ctx, HX_ERR_CUDA, "the fused zeta sweep cannot launch on this device");
         ctx->grid_rk = (int)std::max<long long>(
             1, std::min<long long>(ctx->ntiles[2][ctx->variant[2]], (long long)cps * ctx->num_sms));
@@ -568,9 +570,9 @@ int hx_create(hx_ctx** out, const hx_config* cfg, void* cuda_stream) {
     }
     *out = nullptr;
     if (!(cfg->gamma > 1.0) || (cfg->viscous && (!(cfg->reynolds > 0) || !(cfg->prandtl > 0))) ||
-        (cfg->precision != HX_FP64 && cfg->precision != HX_MIXED) || cfg->scheme != 0 ||
+        (cfg->precision != HX_FP64 && cfg->precision != HX_MIXED) || (cfg->scheme != 0 && cfg->scheme != 1) ||
         (cfg->mu_law != 0 && cfg->mu_law != 1)) {
-        g_create_error = "invalid configuration (gamma > 1, Re, Pr > 0, precision, scheme 0, mu_law 0/1)";
+        g_create_error = "invalid configuration (gamma > 1, Re, Pr > 0, precision, scheme 0/1, mu_law 0/1)";
         return HX_ERR_INVALID_ARG;
     }
     int dev = 0, ndev = 0;

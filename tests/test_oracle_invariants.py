@@ -92,11 +92,12 @@ def test_metric_identity_warped():
 
 # ---------------------------------------------------------------- free stream, conservation
 
-def test_free_stream_preserved_on_warped_grid():
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_free_stream_preserved_on_warped_grid(scheme):
     """Uniform flow on the warped periodic 32^3 grid: R at round-off, and the
-    state stays uniform over 10 RK3 steps."""
+    state stays uniform over 10 RK3 steps (modified and original AFWENO)."""
     w = W.vortex(32, free_stream=True)
-    P = oracle.from_workload(w)
+    P = oracle.from_workload(w, scheme=scheme)
     P.rhs()
     r = P.get_rhs(0)
     q0 = w.blocks[0].q0
@@ -124,13 +125,13 @@ def test_free_stream_preserved_navier_stokes_multiblock():
         assert np.abs(P.get_rhs(bi)).max() < 1e-12
 
 
-@pytest.mark.parametrize("viscous", [False, True])
-def test_discrete_conservation_periodic(viscous):
+@pytest.mark.parametrize("viscous,scheme", [(False, 0), (True, 0), (False, 1)])
+def test_discrete_conservation_periodic(viscous, scheme):
     """Sum of Q/J over a periodic block is constant (Eq. (19) and the viscous
     central differences telescope)."""
     w = W.tgv(16) if viscous else W.vortex(16)
     w.reynolds = 50.0
-    P = oracle.from_workload(w)
+    P = oracle.from_workload(w, scheme=scheme)
     J = P.get_metrics(0)[9]
     tot0 = (w.blocks[0].q0 / J).sum(axis=(1, 2, 3))
     dt, _ = P.dt(0.5)
@@ -320,10 +321,10 @@ def test_tgv_viscous_dissipation_rate():
 
 # ---------------------------------------------------------------- shocks (exact Riemann solution)
 
-def _sod_l1(n, T=0.2):
+def _sod_l1(n, T=0.2, scheme=0):
     import riemann_exact as RE
     w = W.shocktube((n, 6, 6))
-    P = oracle.from_workload(w)
+    P = oracle.from_workload(w, scheme=scheme)
     t = 0.0
     while t < T - 1e-12:
         dt, _ = P.dt(0.5)
@@ -335,6 +336,28 @@ def _sod_l1(n, T=0.2):
     xi = np.where(x >= 1.0, (x - 1.5) / T, (0.5 - x) / T)   # the two tubes, mirror images
     ex = RE.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), G, xi)
     return np.abs(rho - ex[0]).mean(), rho
+
+
+def test_sod_original_afweno_against_exact_riemann_solution():
+    e1, rho = _sod_l1(200, scheme=1)
+    assert e1 < 7.5e-3
+    assert rho.max() < 1.0 + 1e-3 and rho.min() > 0.125 - 1e-3
+
+
+def test_original_afweno_convergence():
+    """Original AFWENO on the warped vortex: error falls at high order (about
+    the modified scheme's) between 32 and 64 nodes."""
+    T = 0.6
+    errs = []
+    for n in (32, 64):
+        w = W.vortex(n, dims=2, nk=6, amp=0.05)
+        P = oracle.from_workload(w, scheme=1)
+        g, _ = P.dt(0.5)
+        ns = int(np.ceil(T / (g * (32.0 / n) ** (2.0 / 3.0))))
+        P.step(ns, T / ns)
+        ex = W.conservative(G, *W.isentropic_vortex(G, w.blocks[0].xyz[0], w.blocks[0].xyz[1], t=T))
+        errs.append(np.sqrt(((P.get_state(0) - ex) ** 2).mean()))
+    assert np.log2(errs[0] / errs[1]) > 3.3
 
 
 def test_sod_shock_tube_against_exact_riemann_solution():
