@@ -386,11 +386,15 @@ def test_original_afweno_parity(name, steps):
 
 def test_original_and_modified_differ_only_by_truncation():
     """The two schemes' residuals differ by a truncation error that falls at
-    high order under refinement (32^3 -> 64^3 on the warped vortex)."""
+    high order under refinement: quasi-2D warped vortex, 64^2 -> 128^2 nodes
+    in the plane (8 spanwise).  On the oracle the ratio is about 37 (5th
+    order would give 32); the bound asks for better than 4th order.  Coarser
+    grids (vortex core over 3 to 6 nodes) are still pre-asymptotic: there the
+    nonlinear weights, not the truncation error, set the difference."""
     d = []
-    for n in (32, 64):
-        w = W.vortex(n)
+    for n in (64, 128):
+        w = W.vortex(n, amp=0.1, dims=2, nk=8)
         a = hx.from_workload(w, scheme=0)
         b = hx.from_workload(w, scheme=1)
         d.append(rel_linf(a.rhs(0), b.rhs(0), "rhs"))
-    assert d[0] > 1e-6 and d[0] / d[1] > 8.0
+    assert d[0] > 1e-6 and d[0] / d[1] > 16.0
