@@ -54,6 +54,7 @@ def load():
         "orc_new": (VP, [P]),
         "orc_add_block": (I, [VP, I, I, I, P]),
         "orc_set_face": (I, [VP, I, I, I, I, I, P]),
+        "orc_set_face_transform": (I, [VP, I, I, ctypes.POINTER(ctypes.c_int)]),
         "orc_check": (I, [VP]),
         "orc_metrics": (I, [VP]),
         "orc_get_metrics": (None, [VP, I, P, I]),
@@ -133,10 +134,15 @@ class Problem:
         self.dims.append((nk, nj, ni))
         return b
 
-    def set_face(self, b, f, kind, nbr=-1, nbr_face=-1, translate=(0.0, 0.0, 0.0)):
+    def set_face(self, b, f, kind, nbr=-1, nbr_face=-1, translate=(0.0, 0.0, 0.0), transform=(1, 2, 3)):
+        """transform: axis a of block b runs along axis |t[a]|-1 of the
+        neighbour, reversed when t[a] < 0 (identity by default)."""
         kind = KIND[kind] if isinstance(kind, str) else int(kind)
         tr = _f64(translate)
         if self._lib.orc_set_face(self._h, b, f, kind, nbr, nbr_face, _p(tr)):
+            raise ValueError("oracle: bad face")
+        tf = (ctypes.c_int * 3)(*[int(t) for t in transform])
+        if self._lib.orc_set_face_transform(self._h, b, f, tf):
             raise ValueError("oracle: bad face")
 
     def check(self):
@@ -203,7 +209,7 @@ def from_workload(w, scheme=0):
         P.add_block(blk.xyz)
     for b, blk in enumerate(w.blocks):
         for f, face in enumerate(blk.faces):
-            P.set_face(b, f, face.kind, face.nbr, face.nbr_face, face.translate)
+            P.set_face(b, f, face.kind, face.nbr, face.nbr_face, face.translate, face.transform)
     P.check()
     P.metrics()
     for b, blk in enumerate(w.blocks):

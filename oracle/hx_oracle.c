@@ -62,6 +62,13 @@
  *       of the face metric; the left-biased value comes from the nodes
  *       i-2..i+2 and the right-biased one from i-1..i+3, each with its own
  *       smoothness indicators.
+ *   R14 1:1 interfaces (Sec. 4.2, Fig. 2 bc_block) may join any face of a
+ *       block to any face of another, with the index axes of the two blocks
+ *       related by a signed permutation (the CGNS 1-to-1 "transform": axis a
+ *       of this block runs along axis |t[a]|-1 of the neighbour, in the same
+ *       direction if t[a] > 0).  The paper's figures show aligned blocks
+ *       only; the state, coordinates and gradients are physical quantities,
+ *       so crossing a face only maps indices.
  * Parity of the physical-face rules (R9, R10) is unpinned: the paper gives no
  * formulas for them.
  */
@@ -76,6 +83,7 @@ enum { OF_PERIODIC = 0, OF_INTERFACE = 1, OF_WALL = 2, OF_FARFIELD = 3, OF_UNSET
 
 typedef struct {
     int kind, nbr, nbr_face;
+    int tf[3];      /* index transform to the neighbour (reading R14)          */
     double tr[3];
 } oface;
 
@@ -352,6 +360,28 @@ static size_t midx(const oblock *B, const int id[3]) {
 
 static int is_phys(int kind) { return kind == OF_WALL || kind == OF_FARFIELD; }
 
+/* Index in the neighbour across face f of block b of the node id, which
+ * lies beyond face f (reading R14).  Layer l = 0, 1, .. beyond the face is
+ * the neighbour's node at distance l from its joined face; the other
+ * directions follow the transform (they may lie outside either block, for
+ * the coordinates of edge and corner ghosts). */
+static void across(const oproblem *P, int b, int f, const int id[3], int nid[3]) {
+    const oblock *B = &P->b[b];
+    const oface *F = &B->f[f];
+    const oblock *N = &P->b[F->nbr];
+    const int d = f / 2, side = f % 2;
+    for (int a = 0; a < 3; ++a) {
+        const int t = F->tf[a], p = abs(t) - 1;
+        if (a == d) {
+            const int l = side ? id[d] - B->n[d] : -1 - id[d];
+            const int nside = F->nbr_face % 2;
+            nid[p] = nside ? N->n[p] - 1 - l : l;
+        } else {
+            nid[p] = t > 0 ? id[a] : N->n[p] - 1 - id[a];
+        }
+    }
+}
+
 /* Coordinates at any index of block b within six layers of its faces
  * (reading R5).  Out-of-range directions are resolved k first, then j, then
  * i: a face neighbour supplies its node (plus the face translation), a
@@ -364,9 +394,8 @@ static void coord_at(const oproblem *P, int b, const int id0[3], double out[3]) 
         const int side = id[d] < 0 ? 0 : 1;
         const oface *F = &B->f[2 * d + side];
         if (!is_phys(F->kind)) {
-            const oblock *N = &P->b[F->nbr];
-            int nid[3] = {id[0], id[1], id[2]};
-            nid[d] = side ? id[d] - B->n[d] : id[d] + N->n[d];
+            int nid[3];
+            across(P, b, 2 * d + side, id, nid);
             double c[3];
             coord_at(P, F->nbr, nid, c);
             for (int m = 0; m < 3; ++m) out[m] = c[m] + F->tr[m];
@@ -410,8 +439,7 @@ static void state_at(const oproblem *P, double *const *Qs, int b, const int id[3
     const oface *F = &B->f[2 * d + side];
     int nid[3] = {id[0], id[1], id[2]};
     if (!is_phys(F->kind)) {
-        const oblock *N = &P->b[F->nbr];
-        nid[d] = side ? id[d] - B->n[d] : id[d] + N->n[d];
+        across(P, b, 2 * d + side, id, nid);
         state_at(P, Qs, F->nbr, nid, q);
     } else if (F->kind == OF_WALL) {
         const int bn = side ? B->n[d] - 1 : 0;
@@ -450,8 +478,8 @@ static void grad_at(const oproblem *P, int b, const int id[3], double g[12]) {
     }
     const int side = id[d] < 0 ? 0 : 1;
     const oface *F = &B->f[2 * d + side];
-    int nid[3] = {id[0], id[1], id[2]};
-    nid[d] = side ? id[d] - B->n[d] : id[d] + P->b[F->nbr].n[d];
+    int nid[3];
+    across(P, b, 2 * d + side, id, nid);
     grad_at(P, F->nbr, nid, g);
 }
 
@@ -905,12 +933,26 @@ int orc_set_face(void *h, int b, int f, int kind, int nbr, int nbr_face, const d
     F->kind = kind;
     F->nbr = nbr;
     F->nbr_face = nbr_face;
+    for (int a = 0; a < 3; ++a) F->tf[a] = a + 1;
     for (int m = 0; m < 3; ++m) F->tr[m] = tr ? tr[m] : 0.0;
     return 0;
 }
 
-/* Checks that every face is set and that face neighbours are the opposite
- * face of the same direction with equal extents across. */
+/* Index transform of face f of block b (reading R14); call after
+ * orc_set_face, whose default is the identity. */
+int orc_set_face_transform(void *h, int b, int f, const int *tf) {
+    oproblem *P = (oproblem *)h;
+    if (b < 0 || b >= P->nb || f < 0 || f > 5) return -1;
+    for (int a = 0; a < 3; ++a) P->b[b].f[f].tf[a] = tf[a];
+    return 0;
+}
+
+/* Checks that every face is set and that each face connection is a
+ * consistent 1:1 join (reading R14): the transform is a signed permutation
+ * with determinant +1 (both blocks keep a right-handed index space), its
+ * normal entry points to the neighbour's face with the sign that the two
+ * sides imply, the neighbour's face points back with the inverse transform,
+ * and the extents along the face agree. */
 int orc_check(void *h) {
     oproblem *P = (oproblem *)h;
     for (int b = 0; b < P->nb; ++b)
@@ -918,11 +960,29 @@ int orc_check(void *h) {
             const oface *F = &P->b[b].f[f];
             if (F->kind == OF_UNSET) return -1;
             if (is_phys(F->kind)) continue;
-            if (F->nbr < 0 || F->nbr >= P->nb) return -1;
-            const int d = f / 2;
-            if (F->nbr_face != (f ^ 1)) return -1;
-            for (int a = 0; a < 3; ++a)
-                if (a != d && P->b[F->nbr].n[a] != P->b[b].n[a]) return -1;
+            if (F->nbr < 0 || F->nbr >= P->nb || F->nbr_face < 0 || F->nbr_face > 5) return -1;
+            const int d = f / 2, side = f % 2, nd = F->nbr_face / 2, nside = F->nbr_face % 2;
+            int seen = 0, M[3][3] = {{0}};
+            for (int a = 0; a < 3; ++a) {
+                const int t = F->tf[a];
+                if (t == 0 || abs(t) > 3) return -1;
+                seen |= 1 << (abs(t) - 1);
+                M[abs(t) - 1][a] = t > 0 ? 1 : -1;
+            }
+            if (seen != 7) return -1;
+            const int det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                            M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                            M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+            if (det != 1) return -1;
+            if (abs(F->tf[d]) - 1 != nd || (F->tf[d] > 0) != (side != nside)) return -1;
+            const oface *Bk = &P->b[F->nbr].f[F->nbr_face];
+            if (is_phys(Bk->kind) || Bk->nbr != b || Bk->nbr_face != f) return -1;
+            for (int a = 0; a < 3; ++a) {
+                const int t = F->tf[a], p = abs(t) - 1;
+                const int u = Bk->tf[p];
+                if (abs(u) - 1 != a || (u > 0) != (t > 0)) return -1;
+                if (a != d && P->b[F->nbr].n[p] != P->b[b].n[a]) return -1;
+            }
         }
     return 0;
 }

@@ -36,6 +36,9 @@ class Face:
     nbr: int = -1
     nbr_face: int = -1
     translate: tuple = (0.0, 0.0, 0.0)   # added to the neighbour's coordinates
+    # axis a of this block runs along axis |transform[a]|-1 of the neighbour,
+    # in the same direction when positive (CGNS 1-to-1 convention)
+    transform: tuple = (1, 2, 3)
 
 
 @dataclass
@@ -188,6 +191,73 @@ def split_state(q, parts):
                 out.append(np.ascontiguousarray(q[:, cuts[2][c]:cuts[2][c + 1], cuts[1][b]:cuts[1][b + 1],
                                                   cuts[0][a]:cuts[0][a + 1]]))
     return out
+
+
+def permute_axes(arr, perm):
+    """Relabels the index axes of a [C][nk][nj][ni] array: old axis c
+    (0 = i, 1 = j, 2 = k) becomes new axis |perm[c]|-1, reversed when
+    perm[c] < 0."""
+    out = np.asarray(arr)
+    for c in range(3):
+        if perm[c] < 0:
+            out = np.flip(out, axis=3 - c)
+    src = {abs(perm[c]) - 1: c for c in range(3)}
+    return np.ascontiguousarray(np.transpose(out, [0] + [3 - src[e] for e in (2, 1, 0)]))
+
+
+def inverse_perm(perm):
+    """The signed permutation that undoes `perm`."""
+    inv = [0, 0, 0]
+    for c in range(3):
+        e = abs(perm[c]) - 1
+        inv[e] = (c + 1) if perm[c] > 0 else -(c + 1)
+    return tuple(inv)
+
+
+def reindex_block(blocks, b, perm):
+    """Relabels the index axes of block b by the signed permutation `perm`
+    (see permute_axes) and rewrites its faces and every face joined to it,
+    so that the grid and the solution are unchanged.  A permutation with
+    determinant -1 would turn the block left-handed (negative Jacobian)."""
+    import copy
+    blocks = [copy.copy(B) for B in blocks]
+    for B in blocks:
+        B.faces = [copy.copy(F) for F in B.faces]
+    B = blocks[b]
+
+    def new_face(f):
+        c, side = f // 2, f % 2
+        e = abs(perm[c]) - 1
+        return 2 * e + (side if perm[c] > 0 else 1 - side)
+
+    sig = [1 if perm[c] > 0 else -1 for c in range(3)]
+    # this block's faces: new position, transform from the new axes
+    faces = [None] * 6
+    for f, F in enumerate(B.faces):
+        c = f // 2
+        G = copy.copy(F)
+        if F.kind in ("periodic", "interface"):
+            t = [0, 0, 0]
+            for cc in range(3):
+                t[abs(perm[cc]) - 1] = sig[cc] * F.transform[cc]
+            G.transform = tuple(t)
+        faces[new_face(f)] = G
+    B.faces = faces
+    B.xyz = permute_axes(B.xyz, perm)
+    if B.q0 is not None:
+        B.q0 = permute_axes(B.q0, perm)
+    # faces that point at this block: neighbour face and target axes
+    for C in blocks:
+        for F in C.faces:
+            if F.kind in ("periodic", "interface") and F.nbr == b:
+                F.nbr_face = new_face(F.nbr_face)
+                t = []
+                for a in range(3):
+                    c = abs(F.transform[a]) - 1
+                    s = 1 if F.transform[a] > 0 else -1
+                    t.append(s * sig[c] * (abs(perm[c])))
+                F.transform = tuple(t)
+    return blocks
 
 
 # ---------------------------------------------------------------------------

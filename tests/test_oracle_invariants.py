@@ -170,6 +170,88 @@ def test_split_box_equals_single_block(parts):
         assert np.abs(P.get_state(bi) - ref[bi]).max() < 1e-13
 
 
+def _rotated_split(w, parts, perms):
+    """w's single periodic block split into `parts`, with the index axes of
+    some blocks relabelled by proper rotations (signed permutations)."""
+    blocks = W.split_periodic_box(w.blocks[0].xyz, w.meta["L"], parts)
+    for B, q in zip(blocks, W.split_state(w.blocks[0].q0, parts)):
+        B.q0 = q
+    for b, perm in perms.items():
+        blocks = W.reindex_block(blocks, b, perm)
+    return blocks
+
+
+ROTATED = [((2, 1, 1), {1: (2, -1, 3)}),
+           ((2, 2, 1), {1: (3, 1, 2), 2: (-1, -2, 3), 3: (1, -3, 2)}),
+           ((1, 1, 2), {0: (-2, 1, 3), 1: (2, 3, 1)})]
+
+
+@pytest.mark.parametrize("parts,perms", ROTATED)
+def test_rotated_blocks_equal_single_block(parts, perms):
+    """1:1 interfaces between blocks whose index axes are permuted and
+    reversed against each other (reading R14): the same grid and state give
+    the same Navier-Stokes solution as the single block, up to the rounding
+    of the reordered sums, once each block's state is mapped back."""
+    w = W.vortex(18, amp=0.1)
+    w.viscous = True
+    w.reynolds = 200.0
+    single = oracle.from_workload(w)
+    dt, _ = single.dt(0.5)
+    single.step(2, dt)
+    ref = W.split_state(single.get_state(0), parts)
+    blocks = _rotated_split(w, parts, perms)
+    P = oracle.Problem(gamma=G, mach=0.5, reynolds=200.0, viscous=True)
+    for B in blocks:
+        P.add_block(B.xyz)
+    for bi, B in enumerate(blocks):
+        for f, F in enumerate(B.faces):
+            P.set_face(bi, f, F.kind, F.nbr, F.nbr_face, F.translate, F.transform)
+    P.check()
+    P.metrics()
+    for bi, B in enumerate(blocks):
+        P.set_state(bi, B.q0)
+    P.step(2, dt)
+    for bi in range(len(blocks)):
+        q = P.get_state(bi)
+        if bi in perms:
+            q = W.permute_axes(q, W.inverse_perm(perms[bi]))
+        assert np.abs(q - ref[bi]).max() < 1e-12, bi
+
+
+def test_reflected_block_is_rejected():
+    """A relabelling with determinant -1 makes the block left-handed; the
+    face transforms that join it are then reflections, which the topology
+    check refuses."""
+    w = W.vortex(12)
+    blocks = _rotated_split(w, (2, 1, 1), {1: (-1, 2, 3)})
+    P = oracle.Problem(gamma=G)
+    for B in blocks:
+        P.add_block(B.xyz)
+    for bi, B in enumerate(blocks):
+        for f, F in enumerate(B.faces):
+            P.set_face(bi, f, F.kind, F.nbr, F.nbr_face, F.translate, F.transform)
+    with pytest.raises(ValueError):
+        P.check()
+
+
+def test_topology_check_rejects_inconsistent_transform():
+    """A face whose neighbour does not point back with the inverse
+    transform is refused."""
+    w = W.vortex(12)
+    blocks = _rotated_split(w, (2, 1, 1), {1: (2, -1, 3)})
+    P = oracle.Problem(gamma=G)
+    for B in blocks:
+        P.add_block(B.xyz)
+    for bi, B in enumerate(blocks):
+        for f, F in enumerate(B.faces):
+            t = F.transform
+            if bi == 0 and f == 1:
+                t = (t[0], -t[1], -t[2])   # still a rotation, but not the inverse of the partner's
+            P.set_face(bi, f, F.kind, F.nbr, F.nbr_face, F.translate, t)
+    with pytest.raises(ValueError):
+        P.check()
+
+
 def test_topology_check_rejects_mismatch():
     w = W.vortex(8)
     P = oracle.Problem(gamma=G)

@@ -40,6 +40,8 @@ MUTANTS = [
     ("closure stencil", "(-3.0 * f[0] + 4.0 * f[1] - f[2]) / 2.0", "(-3.0 * f[0] + 4.0 * f[1] + f[2]) / 2.0"),
     ("far-field invariant", "double Rm = unf - 2.0 * cinf / (g - 1.0);", "double Rm = unf + 2.0 * cinf / (g - 1.0);"),
     ("viscous flux row", "fv[2] = m[0] * txy + m[1] * tyy + m[2] * tyz;", "fv[2] = m[0] * txy + m[1] * tyy + m[2] * txz;"),
+    ("interface tangential flip", "nid[p] = t > 0 ? id[a] : N->n[p] - 1 - id[a];", "nid[p] = id[a];"),
+    ("interface layer", "nid[p] = nside ? N->n[p] - 1 - l : l;", "nid[p] = nside ? N->n[p] - l : l;"),
     ("face flux pairing", "qr[c] = UR[c * L + f + 1 + O];", "qr[c] = UR[c * L + f + O];"),
 ]
 
