@@ -108,13 +108,32 @@ int hx_create(hx_ctx** out, const hx_config* cfg, void* cuda_stream);
 int hx_add_block(hx_ctx* ctx, int ni, int nj, int nk, const double* xyz, int* block_id);
 
 /* Sets face `face` (0..5 = i-, i+, j-, j+, k-, k+) of `block`.  For
- * PERIODIC and INTERFACE faces, nbr_block/nbr_face name the joined face,
- * which must be the opposite face of the same direction (i+ joins i-) with
- * equal extents across; translate (may be NULL = 0) is added to the
- * neighbour's coordinates to give this block's ghost coordinates.  For WALL
- * and FARFIELD the neighbour arguments are ignored. */
+ * PERIODIC and INTERFACE faces (the 1:1 block interfaces of Sec. 4.2 and
+ * Fig. 2, bc_block), nbr_block/nbr_face name the joined face; translate (may
+ * be NULL = 0) is added to the neighbour's coordinates to give this block's
+ * ghost coordinates.  The index transform is reset to the identity (axis a
+ * runs along axis a of the neighbour), which joins i+ to i-, j+ to j- and
+ * k+ to k- of aligned blocks; other pairings need hx_set_face_transform.
+ * A WALL or FARFIELD face needs more than 6 nodes across (the ghost
+ * coordinates reflect through it); the neighbour arguments are ignored.
+ * Checked at hx_finalize (HX_ERR_TOPOLOGY). */
 int hx_set_face(hx_ctx* ctx, int block, int face, int kind, int nbr_block, int nbr_face,
                 const double translate[3]);
+
+/* Index transform of a PERIODIC or INTERFACE face, set after hx_set_face:
+ * axis a (0 = i, 1 = j, 2 = k) of `block` runs along axis
+ * |transform[a]| - 1 of the neighbour, in the same direction when
+ * transform[a] > 0 and reversed when < 0 (the CGNS 1-to-1 convention).
+ * Layer l beyond the face is the neighbour's node at distance l from its
+ * joined face.  hx_finalize requires a rotation (a signed permutation with
+ * determinant +1: both blocks keep a right-handed index space), a normal
+ * entry that reaches nbr_face from the correct side, a neighbour face that
+ * points back with the inverse transform, and equal extents along the
+ * face.  The paper's interfaces are 1:1 but it shows aligned blocks only;
+ * the state, coordinates and gradients are physical quantities, so the
+ * transform maps indices and nothing else.  Entries outside +-1..+-3:
+ * HX_ERR_INVALID_ARG; after hx_finalize: HX_ERR_STATE. */
+int hx_set_face_transform(hx_ctx* ctx, int block, int face, const int transform[3]);
 
 /* Validates the topology (HX_ERR_TOPOLOGY), plans device buffers and work
  * lists and allocates them (HX_ERR_OOM). */

@@ -28,6 +28,10 @@ struct DevBlock {
     int wall;         // bit f: face f is a wall
     int ff;           // bit f: face f is a far field
     int nbr[6];       // block joined across face f (periodic / interface), -1 on physical faces
+    // index transform of face f (1:1 interface, Sec. 4.2): axis a of this
+    // block runs along axis |tf[f][a]|-1 of the neighbour, reversed when
+    // negative (the CGNS 1-to-1 convention); identity for aligned blocks
+    signed char tf[6][3];
     double dt;        // time step of this block
 };
 
@@ -80,6 +84,51 @@ __host__ __device__ inline long long node_index(const DevBlock& B, int i, int j,
     return B.base + i + (long long)j * B.sj + (long long)k * B.sk;
 }
 
+// Index in the neighbour N (extents nN) across face f of block B of the
+// index id of B, which lies beyond face f: layer l = 0, 1, .. beyond the
+// face is N's node at distance l from its joined face; the other directions
+// follow the face transform (they may lie outside either block, for the
+// coordinates of edge and corner ghosts).
+__host__ __device__ inline void across_face(const DevBlock& B, const int nN[3], int f, const int id[3], int out[3]) {
+    const int d = f >> 1, side = f & 1;
+    int v[3], p[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int t = B.tf[f][a];
+        p[a] = (t < 0 ? -t : t) - 1;
+        if (a == d) {
+            const int l = side ? id[d] - B.n[d] : -1 - id[d];
+            const int nside = t > 0 ? 1 - side : side;
+            v[a] = nside ? nN[p[a]] - 1 - l : l;
+        } else {
+            v[a] = t > 0 ? id[a] : nN[p[a]] - 1 - id[a];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) out[q] = p[0] == q ? v[0] : (p[1] == q ? v[1] : v[2]);
+}
+
+// The face ghost of N that node id of B (at distance s from face f) fills:
+// the inverse of across_face.
+__device__ __forceinline__ void ghost_across(const DevBlock& B, const DevBlock& N, int f, int s, const int id[3],
+                                             int out[3]) {
+    const int d = f >> 1, side = f & 1;
+    int v[3], p[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int t = B.tf[f][a];
+        p[a] = (t < 0 ? -t : t) - 1;
+        if (a == d) {
+            const int nside = t > 0 ? 1 - side : side;
+            v[a] = nside ? N.n[p[a]] + s : -1 - s;
+        } else {
+            v[a] = t > 0 ? id[a] : N.n[p[a]] - 1 - id[a];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) out[q] = p[0] == q ? v[0] : (p[1] == q ? v[1] : v[2]);
+}
+
 // Halo by push: node id of block B sends its values `vals` (nf fields) to
 // the face ghosts they fill in the blocks joined across its faces (nodes
 // within G of a periodic or interface face), and, with `mirror`, to B's own
@@ -97,7 +146,7 @@ __device__ __forceinline__ void push_ghosts(const DevBlock* __restrict__ blocks,
         if (B.nbr[f] >= 0) {
             if (s < G) {
                 const DevBlock& N = blocks[B.nbr[f]];
-                t[d] = side ? -1 - s : N.n[d] + s;
+                ghost_across(B, N, f, s, id, t);
                 const long long e = node_index(N, t[0], t[1], t[2]);
                 for (int c = 0; c < nf; ++c) arr[c * fs + e] = vals[c];
             }

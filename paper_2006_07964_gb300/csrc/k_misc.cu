@@ -190,7 +190,7 @@ k_prep(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
             int src[3] = {i, j, k};
             if (B.nbr[f] >= 0) {   // periodic / interface: the joined block's node
                 const DevBlock& N = blocks[B.nbr[f]];
-                src[d] = side ? id[d] - B.n[d] : id[d] + N.n[d];
+                across_face(B, N.n, f, id, src);
                 const long long es = node_index(N, src[0], src[1], src[2]);
                 for (int c = 0; c < 5; ++c) q[c] = Q[c * fs + es];
             } else if ((B.wall >> f) & 1) {   // wall mirror through the boundary node

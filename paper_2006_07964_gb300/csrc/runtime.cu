@@ -22,6 +22,7 @@ thread_local std::string g_create_error;
 
 struct HostFace {
     int kind = -1, nbr = -1, nbr_face = -1;
+    int tf[3] = {1, 2, 3};     // index transform to the neighbour (identity: aligned blocks)
     double tr[3] = {0, 0, 0};
 };
 
@@ -154,45 +155,52 @@ void add_bricks(std::vector<Brick>& out, int b, const int lo[3], const int hi[3]
                 out.push_back(Brick{b, i, j, k, std::min(32, hi[0] - i), std::min(8, hi[1] - j), 1, 0});
 }
 
-// Coordinate ghost items of pass d (directions < d already carry ghosts).
-void coord_halo_items(const hx_ctx* ctx, int d, std::vector<HaloItem>& out) {
+// Coordinate ghost items of pass m: the ghost nodes (within GC of the
+// block) that lie outside it in exactly m directions.  Each resolves its
+// highest out-of-range direction d: across a periodic or interface face it
+// copies the neighbour's node (plus the face translation), which lies
+// outside the neighbour in m-1 directions; on a physical face it reflects
+// through the boundary node (m-1 again).  Pass m therefore reads only what
+// passes < m wrote, and edges and corners resolve k first, then j, then i.
+void coord_halo_items(const hx_ctx* ctx, int m, std::vector<HaloItem>& out) {
     for (int b = 0; b < (int)ctx->blocks.size(); ++b) {
         const HostBlock& H = ctx->blocks[b];
-        for (int side = 0; side < 2; ++side) {
-            const int f = 2 * d + side;
-            const HostFace& F = H.f[f];
-            int lo[3], hi[3];
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = a < d ? -GC : 0;
-                hi[a] = a < d ? H.n[a] + GC : H.n[a];
+        auto in = [&](int a, int x) { return x >= 0 && x < H.n[a]; };
+        for (int k = -GC; k < H.n[2] + GC; ++k)
+            for (int j = -GC; j < H.n[1] + GC; ++j) {
+                const int cjk = !in(1, j) + !in(2, k);
+                if (cjk > m || cjk < m - 1) continue;
+                for (int i = -GC; i < H.n[0] + GC; ++i) {
+                    if (cjk == m && !in(0, i)) continue;
+                    if (cjk == m - 1 && in(0, i)) {
+                        i = H.n[0] - 1;   // skip the interior run
+                        continue;
+                    }
+                    const int g[3] = {i, j, k};
+                    int d = 2;
+                    while (in(d, g[d])) --d;
+                    const int side = g[d] < 0 ? 0 : 1, f = 2 * d + side;
+                    const HostFace& F = H.f[f];
+                    HaloItem it{};
+                    it.dst = (int)nidx(H.cdev, g);
+                    if (!is_phys(F.kind)) {
+                        const HostBlock& N = ctx->blocks[F.nbr];
+                        int src[3];
+                        across_face(H.dev, N.n, f, g, src);
+                        it.src = (int)nidx(N.cdev, src);
+                        it.mode = HM_TRANSLATE | ((b * 6 + f) << 8);
+                    } else {
+                        const int bnd = side ? H.n[d] - 1 : 0;
+                        int bn[3] = {i, j, k}, src[3] = {i, j, k};
+                        bn[d] = bnd;
+                        src[d] = 2 * bnd - g[d];
+                        it.src = (int)nidx(H.cdev, src);
+                        it.aux = (int)nidx(H.cdev, bn);
+                        it.mode = HM_REFLECT;
+                    }
+                    out.push_back(it);
+                }
             }
-            const int n = H.n[d];
-            for (int s = 1; s <= GC; ++s) {
-                lo[d] = hi[d] = 0;
-                for (int k = (d == 2 ? 0 : lo[2]); k < (d == 2 ? 1 : hi[2]); ++k)
-                    for (int j = (d == 1 ? 0 : lo[1]); j < (d == 1 ? 1 : hi[1]); ++j)
-                        for (int i = (d == 0 ? 0 : lo[0]); i < (d == 0 ? 1 : hi[0]); ++i) {
-                            int g[3] = {i, j, k}, src[3] = {i, j, k};
-                            g[d] = side ? n - 1 + s : -s;
-                            HaloItem it{};
-                            it.dst = (int)nidx(H.cdev, g);
-                            if (!is_phys(F.kind)) {
-                                const HostBlock& N = ctx->blocks[F.nbr];
-                                src[d] = side ? s - 1 : N.n[d] - s;
-                                it.src = (int)nidx(N.cdev, src);
-                                it.mode = HM_TRANSLATE | ((b * 6 + f) << 8);
-                            } else {
-                                int bn[3] = {i, j, k};
-                                bn[d] = side ? n - 1 : 0;
-                                src[d] = side ? n - 1 - s : s;
-                                it.src = (int)nidx(H.cdev, src);
-                                it.aux = (int)nidx(H.cdev, bn);
-                                it.mode = HM_REFLECT;
-                            }
-                            out.push_back(it);
-                        }
-            }
-        }
     }
 }
 
@@ -627,7 +635,20 @@ int hx_set_face(hx_ctx* ctx, int block, int face, int kind, int nbr_block, int n
     F.kind = kind;
     F.nbr = nbr_block;
     F.nbr_face = nbr_face;
+    for (int a = 0; a < 3; ++a) F.tf[a] = a + 1;
     for (int m = 0; m < 3; ++m) F.tr[m] = translate ? translate[m] : 0.0;
+    return HX_OK;
+}
+
+int hx_set_face_transform(hx_ctx* ctx, int block, int face, const int transform[3]) {
+    if (!ctx) return HX_ERR_INVALID_ARG;
+    if (ctx->finalized) return fail(ctx, HX_ERR_STATE, "hx_set_face_transform after hx_finalize");
+    if (block < 0 || block >= (int)ctx->blocks.size() || face < 0 || face > 5 || !transform)
+        return fail(ctx, HX_ERR_INVALID_ARG, "bad block, face or transform");
+    for (int a = 0; a < 3; ++a)
+        if (transform[a] == 0 || transform[a] < -3 || transform[a] > 3)
+            return fail(ctx, HX_ERR_INVALID_ARG, "transform entries must be +-1, +-2 or +-3");
+    for (int a = 0; a < 3; ++a) ctx->blocks[block].f[face].tf[a] = transform[a];
     return HX_OK;
 }
 
@@ -647,10 +668,36 @@ int hx_finalize(hx_ctx* ctx) {
                 std::snprintf(msg, sizeof msg, "block %d face %d not set", b, f);
                 return fail(ctx, HX_ERR_TOPOLOGY, msg);
             }
-            if (is_phys(F.kind)) continue;
-            const int d = f / 2;
-            if (F.nbr < 0 || F.nbr >= nb || F.nbr_face != (f ^ 1)) {
-                std::snprintf(msg, sizeof msg, "block %d face %d: neighbour must be the opposite face of a block", b, f);
+            const int d = f / 2, side = f % 2;
+            if (is_phys(F.kind)) {
+                if (ctx->blocks[b].n[d] <= GC) {
+                    std::snprintf(msg, sizeof msg, "block %d face %d: a physical face needs more than %d nodes "
+                                  "across", b, f, GC);
+                    return fail(ctx, HX_ERR_TOPOLOGY, msg);
+                }
+                continue;
+            }
+            if (F.nbr < 0 || F.nbr >= nb || F.nbr_face < 0 || F.nbr_face > 5) {
+                std::snprintf(msg, sizeof msg, "block %d face %d: bad neighbour block or face", b, f);
+                return fail(ctx, HX_ERR_TOPOLOGY, msg);
+            }
+            // the transform: a rotation of the index axes (signed permutation,
+            // determinant +1) whose normal entry reaches the neighbour's face
+            // from the correct side
+            int used = 0, M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            for (int a = 0; a < 3; ++a) {
+                const int t = F.tf[a], p = std::abs(t) - 1;
+                used |= 1 << p;
+                M[p][a] = t > 0 ? 1 : -1;
+            }
+            const int det = used != 7 ? 0
+                            : M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                                  M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                                  M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+            const int nside = F.nbr_face % 2;
+            if (det != 1 || std::abs(F.tf[d]) - 1 != F.nbr_face / 2 || (F.tf[d] > 0) != (side != nside)) {
+                std::snprintf(msg, sizeof msg, "block %d face %d: the transform is not a rotation that joins "
+                              "face %d of block %d", b, f, F.nbr_face, F.nbr);
                 return fail(ctx, HX_ERR_TOPOLOGY, msg);
             }
             const HostBlock &H = ctx->blocks[b], &N = ctx->blocks[F.nbr];
@@ -659,11 +706,18 @@ int hx_finalize(hx_ctx* ctx) {
                 std::snprintf(msg, sizeof msg, "block %d face %d: neighbour face does not point back", b, f);
                 return fail(ctx, HX_ERR_TOPOLOGY, msg);
             }
-            for (int a = 0; a < 3; ++a)
-                if (a != d && H.n[a] != N.n[a]) {
+            for (int a = 0; a < 3; ++a) {
+                const int t = F.tf[a], p = std::abs(t) - 1, u = back.tf[p];
+                if (std::abs(u) - 1 != a || (u > 0) != (t > 0)) {
+                    std::snprintf(msg, sizeof msg, "block %d face %d: the neighbour's transform is not the inverse",
+                                  b, f);
+                    return fail(ctx, HX_ERR_TOPOLOGY, msg);
+                }
+                if (a != d && H.n[a] != N.n[p]) {
                     std::snprintf(msg, sizeof msg, "block %d face %d: extents across differ from the neighbour", b, f);
                     return fail(ctx, HX_ERR_TOPOLOGY, msg);
                 }
+            }
         }
     // ---- layouts
     long long off = 0, offc = 0;
@@ -688,6 +742,7 @@ int hx_finalize(hx_ctx* ctx) {
             if (H.f[f].kind == HX_FACE_WALL) H.dev.wall |= 1 << f;
             if (H.f[f].kind == HX_FACE_FARFIELD) H.dev.ff |= 1 << f;
             H.dev.nbr[f] = is_phys(H.f[f].kind) ? -1 : H.f[f].nbr;
+            for (int a = 0; a < 3; ++a) H.dev.tf[f][a] = (signed char)(is_phys(H.f[f].kind) ? a + 1 : H.f[f].tf[a]);
         }
         H.dev.dt = 0.0;
         ctx->max_block_pts = std::max(ctx->max_block_pts, H.npts());
@@ -822,9 +877,9 @@ int hx_compute_metrics(hx_ctx* ctx) {
     if ((rc = upload(ctx, &dtr, tr))) return rc;
     if ((rc = upload(ctx, &dc, ctab))) return rc;
     std::vector<std::pair<void*, size_t>> tmp;
-    for (int d = 0; d < 3; ++d) {
+    for (int m = 1; m <= 3; ++m) {
         std::vector<HaloItem> items;
-        coord_halo_items(ctx, d, items);
+        coord_halo_items(ctx, m, items);
         HaloItem* di = nullptr;
         if ((rc = upload(ctx, &di, items))) return rc;
         tmp.emplace_back((void*)di, items.size() * sizeof(HaloItem));

@@ -31,6 +31,7 @@ EXPORTS = (
     "hx_set_state", "hx_get_state", "hx_get_metrics", "hx_compute_dt", "hx_step", "hx_step_multi", "hx_rhs",
     "hx_get_gradients", "hx_profile_step", "hx_launches_per_step", "hx_points", "hx_device_bytes",
     "hx_last_error", "hx_destroy", "hx_euler_rhs_periodic_noalloc", "hx_tuning", "hx_step_cfl", "hx_residual",
+    "hx_set_face_transform",
 )
 
 
@@ -73,6 +74,7 @@ def load(path=None):
         "hx_create": (I, [ctypes.POINTER(CTX), ctypes.POINTER(hx_config), VP]),
         "hx_add_block": (I, [CTX, I, I, I, VP, ctypes.POINTER(I)]),
         "hx_set_face": (I, [CTX, I, I, I, I, I, P]),
+        "hx_set_face_transform": (I, [CTX, I, I, ctypes.POINTER(ctypes.c_int)]),
         "hx_finalize": (I, [CTX]),
         "hx_compute_metrics": (I, [CTX]),
         "hx_set_state": (I, [CTX, I, VP, I]),
@@ -171,10 +173,15 @@ class Context:
         self.dims.append((nk, nj, ni))
         return bid.value
 
-    def set_face(self, block, face, kind, nbr=-1, nbr_face=-1, translate=(0.0, 0.0, 0.0)):
+    def set_face(self, block, face, kind, nbr=-1, nbr_face=-1, translate=(0.0, 0.0, 0.0), transform=None):
+        """transform: axis a of `block` runs along axis |t[a]|-1 of the
+        neighbour, reversed when t[a] < 0 (None: identity)."""
         kind = FACE[kind] if isinstance(kind, str) else int(kind)
         tr = np.ascontiguousarray(translate, dtype=np.float64)
         self._check(self._lib.hx_set_face(self._h, block, face, kind, nbr, nbr_face, _dp(tr)))
+        if transform is not None and tuple(transform) != (1, 2, 3):
+            tf = (ctypes.c_int * 3)(*[int(t) for t in transform])
+            self._check(self._lib.hx_set_face_transform(self._h, block, face, tf))
 
     def finalize(self):
         self._check(self._lib.hx_finalize(self._h))
@@ -306,7 +313,7 @@ def from_workload(w, precision="fp64", stream=None, autotune=1, mem_cap_bytes=0,
         ctx.add_block(blk.xyz)
     for b, blk in enumerate(w.blocks):
         for f, face in enumerate(blk.faces):
-            ctx.set_face(b, f, face.kind, face.nbr, face.nbr_face, face.translate)
+            ctx.set_face(b, f, face.kind, face.nbr, face.nbr_face, face.translate, face.transform)
     ctx.finalize()
     ctx.compute_metrics()
     for b, blk in enumerate(w.blocks):

@@ -70,6 +70,16 @@ def split(w, parts):
                       prandtl=w.prandtl, viscous=w.viscous, mu_law=w.mu_law)
 
 
+def rotated(w, parts, perms):
+    """split(w, parts) with the index axes of some blocks relabelled by
+    rotations, so that their interfaces join permuted and reversed axes."""
+    ws = split(w, parts)
+    for b, perm in perms.items():
+        ws.blocks = W.reindex_block(ws.blocks, b, perm)
+    ws.name = w.name + "_rotated"
+    return ws
+
+
 CASES = {
     "vortex32": lambda: W.vortex(32),
     "ragged_euler": lambda: warped((37, 29, 23)),
@@ -79,6 +89,9 @@ CASES = {
     "ogrid_s4": lambda: W.ogrid(scale=4),
     "ogrid_s8": lambda: W.ogrid(scale=8),
     "shock_warped": lambda: W.shocktube((96, 12, 12), amp=0.04),
+    "rotated_euler": lambda: rotated(warped((28, 24, 20)), (2, 2, 1), {1: (3, 1, 2), 2: (-1, -2, 3), 3: (1, -3, 2)}),
+    "rotated_ns": lambda: rotated(warped((24, 22, 26), viscous=True, reynolds=100.0), (1, 1, 2),
+                                  {0: (-2, 1, 3), 1: (2, 3, 1)}),
 }
 
 
@@ -89,7 +102,7 @@ def pair(name, precision="fp64"):
 
 # ---------------------------------------------------------------- metrics, dt
 
-@pytest.mark.parametrize("name", ["vortex32", "ragged_euler", "split_ns", "ogrid_s4"])
+@pytest.mark.parametrize("name", ["vortex32", "ragged_euler", "split_ns", "ogrid_s4", "rotated_euler", "rotated_ns"])
 def test_metrics_parity(name):
     w, ctx, P = pair(name)
     for b in range(len(w.blocks)):
@@ -115,7 +128,7 @@ def test_rhs_parity(name):
         assert rel_linf(ctx.rhs(b), P.get_rhs(b), "rhs") < TOL_RHS, (name, b)
 
 
-@pytest.mark.parametrize("name", ["ragged_ns", "tgv24", "split_ns", "ogrid_s8"])
+@pytest.mark.parametrize("name", ["ragged_ns", "tgv24", "split_ns", "ogrid_s8", "rotated_ns"])
 def test_gradient_parity(name):
     w, ctx, P = pair(name)
     P.rhs()
@@ -133,7 +146,8 @@ def test_free_stream_residual_gpu():
 # ---------------------------------------------------------------- steps
 
 @pytest.mark.parametrize("name,steps", [("vortex32", 10), ("ragged_euler", 4), ("tgv24", 5), ("split_ns", 3),
-                                        ("ogrid_s4", 5), ("shock_warped", 20)])
+                                        ("ogrid_s4", 5), ("shock_warped", 20), ("rotated_euler", 4),
+                                        ("rotated_ns", 3)])
 def test_steps_parity(name, steps):
     w, ctx, P = pair(name)
     dt, _ = P.dt(0.5)
@@ -275,6 +289,25 @@ def test_error_topology():
     with pytest.raises(hx.HxError) as ei:
         ctx.finalize()
     assert ei.value.name == "HX_ERR_TOPOLOGY"
+
+
+def test_error_topology_reflected_interface():
+    """Relabelling one block's axes by a reflection turns the transforms of
+    its interfaces into reflections, which hx_finalize refuses; a transform
+    entry out of range is refused at once."""
+    w = rotated(warped((16, 12, 12)), (2, 1, 1), {1: (-1, 2, 3)})
+    ctx = hx.Context()
+    for B in w.blocks:
+        ctx.add_block(B.xyz)
+    for b, B in enumerate(w.blocks):
+        for f, F in enumerate(B.faces):
+            ctx.set_face(b, f, F.kind, F.nbr, F.nbr_face, F.translate, F.transform)
+    with pytest.raises(hx.HxError) as ei:
+        ctx.finalize()
+    assert ei.value.name == "HX_ERR_TOPOLOGY"
+    with pytest.raises(hx.HxError) as ei:
+        ctx.set_face(0, 1, "interface", 1, 0, (0, 0, 0), (1, 4, 3))
+    assert ei.value.name == "HX_ERR_INVALID_ARG"
 
 
 def test_error_bad_grid():
