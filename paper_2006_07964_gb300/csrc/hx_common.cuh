@@ -108,15 +108,16 @@ __host__ __device__ inline void across_face(const DevBlock& B, const int nN[3], 
     for (int q = 0; q < 3; ++q) out[q] = p[0] == q ? v[0] : (p[1] == q ? v[1] : v[2]);
 }
 
-// The face ghost of N that node id of B (at distance s from face f) fills:
-// the inverse of across_face.
-__device__ __forceinline__ void ghost_across(const DevBlock& B, const DevBlock& N, int f, int s, const int id[3],
-                                             int out[3]) {
+// The face ghost of N that a node (indices id, at distance s from face f
+// of its block) fills: the inverse of across_face.  tf is the face's
+// transform, read from the block table where the push needs it.
+__device__ __forceinline__ void ghost_across(const signed char* tf, const DevBlock& N, int f, int s,
+                                             const int id[3], int out[3]) {
     const int d = f >> 1, side = f & 1;
     int v[3], p[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int t = B.tf[f][a];
+        const int t = tf[a];
         p[a] = (t < 0 ? -t : t) - 1;
         if (a == d) {
             const int nside = t > 0 ? 1 - side : side;
@@ -136,8 +137,8 @@ __device__ __forceinline__ void ghost_across(const DevBlock& B, const DevBlock& 
 // negated).  Each ghost has exactly one sender, so no synchronisation is
 // needed; the ghosts are ready for the next kernel on the stream.
 template <class T>
-__device__ __forceinline__ void push_ghosts(const DevBlock* __restrict__ blocks, const DevBlock& B, const int id[3],
-                                            T* arr, long long fs, int nf, const T* vals, bool mirror) {
+__device__ __forceinline__ void push_ghosts(const DevBlock* __restrict__ blocks, const DevBlock& B, int bidx,
+                                            const int id[3], T* arr, long long fs, int nf, const T* vals, bool mirror) {
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
         const int d = f >> 1, side = f & 1;
@@ -146,7 +147,7 @@ __device__ __forceinline__ void push_ghosts(const DevBlock* __restrict__ blocks,
         if (B.nbr[f] >= 0) {
             if (s < G) {
                 const DevBlock& N = blocks[B.nbr[f]];
-                ghost_across(B, N, f, s, id, t);
+                ghost_across(blocks[bidx].tf[f], N, f, s, id, t);
                 const long long e = node_index(N, t[0], t[1], t[2]);
                 for (int c = 0; c < nf; ++c) arr[c * fs + e] = vals[c];
             }
@@ -238,33 +239,47 @@ __device__ __forceinline__ R viscosity(const GasR<R>& g, R T) {
 // 5/8, 5/16 for the stencils {i-2..i}, {i-1..i+1}, {i..i+2} (left value),
 // mirrored for the right value.
 // ---------------------------------------------------------------------------
+//
+// FP64 runs at 1/64 of the FP32 rate here, so the FP64 form is written for
+// the fewest FP64 instructions; in exact arithmetic it gives the same values:
+//   - a_k are the second differences and c_k the remaining Eq. (17) terms,
+//     both from the first differences;
+//   - s_k = 4 (eps + beta_k) = 4 eps + (13/3) a_k^2 + c_k^2 (a common factor
+//     of the s_k cancels in the normalised weights), and gamma/s^2 scaled by
+//     16 s1^2 s2^2 s3^2 gives the unnormalised weights (p23, 10 p13, 5 p12)
+//     of the left value and (p12, 10 p13, 5 p23) of the right one,
+//     p_jk = s_j^2 s_k^2;
+//   - since the weights sum to one, each value is the central candidate plus
+//     weighted differences of the outer candidates, which are third
+//     differences: uL1 - uL2 = 3 e1 / 8, uL3 - uL2 = e2 / 8 with
+//     e1 = a1 - a2 = w0 - 3w1 + 3w2 - w3, e2 = a2 - a3 (mirrored for the right
+//     value), so left = uL2 + (3 p23 e1 + 5 p12 e2) / (8 dL) and
+//     right = uR2 - (3 p12 e2 + 5 p23 e1) / (8 dR).
 __device__ __forceinline__ void weno_pair(double w0, double w1, double w2, double w3, double w4,
                                           double& left, double& right) {
-    const double eps = 1.0e-6;
-    const double a1 = w0 - 2.0 * w1 + w2, c1 = w0 - 4.0 * w1 + 3.0 * w2;
-    const double a2 = w1 - 2.0 * w2 + w3, c2 = w1 - w3;
-    const double a3 = w2 - 2.0 * w3 + w4, c3 = 3.0 * w2 - 4.0 * w3 + w4;
-    const double b1 = (13.0 / 12.0) * a1 * a1 + 0.25 * c1 * c1;
-    const double b2 = (13.0 / 12.0) * a2 * a2 + 0.25 * c2 * c2;
-    const double b3 = (13.0 / 12.0) * a3 * a3 + 0.25 * c3 * c3;
-    double s1 = eps + b1, s2 = eps + b2, s3 = eps + b3;
+    const double eps4 = 4.0e-6;
+    const double d10 = w1 - w0, d21 = w2 - w1, d32 = w3 - w2, d43 = w4 - w3;
+    const double a1 = d21 - d10, a2 = d32 - d21, a3 = d43 - d32;
+    const double c1 = fma(2.0, d21, a1), c2 = d21 + d32, c3 = fma(-2.0, d32, a3);
+    const double k = 13.0 / 3.0;
+    double s1 = fma(a1, k * a1, fma(c1, c1, eps4));
+    double s2 = fma(a2, k * a2, fma(c2, c2, eps4));
+    double s3 = fma(a3, k * a3, fma(c3, c3, eps4));
     s1 *= s1;
     s2 *= s2;
     s3 *= s3;
-    // gamma_j / s_j normalised == gamma_j * prod_{k != j} s_k normalised
     const double p12 = s1 * s2, p13 = s1 * s3, p23 = s2 * s3;
-    const double uL1 = 0.375 * w0 - 1.25 * w1 + 1.875 * w2;
-    const double uL2 = -0.125 * w1 + 0.75 * w2 + 0.375 * w3;
-    const double uL3 = 0.375 * w2 + 0.75 * w3 - 0.125 * w4;
-    const double uR1 = 0.375 * w4 - 1.25 * w3 + 1.875 * w2;
-    const double uR2 = -0.125 * w3 + 0.75 * w2 + 0.375 * w1;
-    const double uR3 = 0.375 * w2 + 0.75 * w1 - 0.125 * w0;
-    const double tL1 = 0.0625 * p23, tL2 = 0.625 * p13, tL3 = 0.3125 * p12;
-    const double tR1 = 0.0625 * p12, tR2 = 0.625 * p13, tR3 = 0.3125 * p23;
-    const double dL = tL1 + tL2 + tL3, dR = tR1 + tR2 + tR3;
-    const double inv = 1.0 / (dL * dR);   // one division for both weight sets
-    left = (tL1 * uL1 + tL2 * uL2 + tL3 * uL3) * (dR * inv);
-    right = (tR1 * uR1 + tR2 * uR2 + tR3 * uR3) * (dL * inv);
+    const double dL = fma(10.0, p13, fma(5.0, p12, p23));
+    const double dR = fma(10.0, p13, fma(5.0, p23, p12));
+    const double e1 = a1 - a2, e2 = a2 - a3;
+    const double A = p23 * e1, B = p12 * e2;
+    const double nL = fma(3.0, A, 5.0 * B), nR = fma(3.0, B, 5.0 * A);
+    const double m2 = 0.75 * w2;
+    const double uL2 = fma(0.375, w3, fma(-0.125, w1, m2));
+    const double uR2 = fma(0.375, w1, fma(-0.125, w3, m2));
+    const double inv = 0.125 / (dL * dR);   // one division for both values
+    left = fma(nL, dR * inv, uL2);
+    right = fma(-nR, dL * inv, uR2);
 }
 
 __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3, float w4, float& left,
@@ -337,8 +352,79 @@ __device__ __forceinline__ R weno_one(R w0, R w1, R w2, R w3, R w4) {
 //   U_4 = |u|^2/2 Wk + rho u.C + al (s H + c theta t),  al = rho/(sqrt(2) c),
 // which is the matrix pair L = T_k^-1, R = T_k entry by entry.
 // ---------------------------------------------------------------------------
+// FP64: per-node products are hoisted out of the five stencil projections
+// (the FP64 pipe is the bound; registers are not).
 template <class R>
 struct CharBasis {
+    R kx, ky, kz, u, v, w, rho, irho, p, c, a0, g, gu, gv, gw, cir, kxi, kyi, kzi, kxs, kys, kzs, al, alc, acth,
+        half_uu, H;
+    __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
+        irho = hrcp(q[0]);
+        rho = q[0];
+        u = q[1] * irho;
+        v = q[2] * irho;
+        w = q[3] * irho;
+        half_uu = R(0.5) * (u * u + v * v + w * w);
+        p = gs.gm1 * (q[4] - rho * half_uu);
+        const R c2 = gs.gamma * p * irho;
+        const R ic = hrsqrt(c2);
+        c = c2 * ic;
+        const R imm = hrsqrt(mx * mx + my * my + mz * mz);
+        kx = mx * imm;
+        ky = my * imm;
+        kz = mz * imm;
+        const R phi2 = gs.gm1 * half_uu;
+        const R ic2 = ic * ic;
+        a0 = R(1) - phi2 * ic2;
+        g = gs.gm1 * ic2;
+        gu = g * u;
+        gv = g * v;
+        gw = g * w;
+        // the projection works on rho d = (Q_m - u_m Q_0); 1/rho and 1/sqrt(2)
+        // go into the normal once per node
+        kxi = kx * irho;
+        kyi = ky * irho;
+        kzi = kz * irho;
+        kxs = kxi * R(0.70710678118654752440);
+        kys = kyi * R(0.70710678118654752440);
+        kzs = kzi * R(0.70710678118654752440);
+        cir = c * irho * R(0.70710678118654752440);
+        al = rho * ic * R(0.70710678118654752440);
+        alc = al * c;
+        H = half_uu + c2 * gs.inv_gm1;
+        acth = alc * (kx * u + ky * v + kz * w);
+    }
+    // W = L q
+    __device__ __forceinline__ void project(R q0, R q1, R q2, R q3, R q4, R W[5]) const {
+        const R d1 = q1 - u * q0, d2 = q2 - v * q0, d3 = q3 - w * q0;
+        const R S = a0 * q0 + gu * q1 + gv * q2 + gw * q3 - g * q4;
+        W[0] = kx * S + (d2 * kzi - d3 * kyi);
+        W[1] = ky * S + (d3 * kxi - d1 * kzi);
+        W[2] = kz * S + (d1 * kyi - d2 * kxi);
+        const R kd = kxs * d1 + kys * d2 + kzs * d3;
+        const R base = cir * (q0 - S);
+        W[3] = base + kd;
+        W[4] = base - kd;
+    }
+    // U = R W
+    __device__ __forceinline__ void back(const R W[5], R U[5]) const {
+        const R Wk = kx * W[0] + ky * W[1] + kz * W[2];
+        const R Cx = ky * W[2] - kz * W[1], Cy = kz * W[0] - kx * W[2], Cz = kx * W[1] - ky * W[0];
+        const R s = W[3] + W[4], t = W[3] - W[4];
+        const R as = al * s, act = alc * t;
+        U[0] = Wk + as;
+        U[1] = u * U[0] + (rho * Cx + act * kx);
+        U[2] = v * U[0] + (rho * Cy + act * ky);
+        U[3] = w * U[0] + (rho * Cz + act * kz);
+        U[4] = half_uu * Wk + rho * (u * Cx + v * Cy + w * Cz) + as * H + acth * t;
+    }
+};
+
+// FP32 (mixed form): the same basis with fewer per-node members, which keeps
+// the sweep kernels within their register budget; FP32 arithmetic is cheap.
+template <>
+struct CharBasis<float> {
+    using R = float;
     R kx, ky, kz, u, v, w, rho, irho, p, c, a0, g, cir, al, half_uu, H, cth;
     __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
         irho = hrcp(q[0]);

@@ -29,13 +29,16 @@ template <int DIR, int TP, int NA>
 struct FluxLayout {
     static constexpr int RING = TP >= 8 ? 2 * TP : 16;   // >= TP + 6 live nodes, power of two
     // DIR 0 sweeps the contiguous i: lanes run along the sweep and planes are
-    // [line][slot] (one pad); DIR 1, 2: lanes run across (i), planes [slot][line].
-    static constexpr int PLANE = DIR == 0 ? NA * (RING + 1) : RING * NA;
+    // [line][slot]; a warp spans two lines of 16 nodes when TP = 16, so odd
+    // lines swap the two halves of their ring (slot ^ RING/2) and the two
+    // half-warps fall on complementary banks.  DIR 1, 2: lanes run across
+    // (i), planes [slot][line].
+    static constexpr int PLANE = RING * NA;
     // fields per ring slot: Q 5, metric 3, node flux 5, U^L (then h) 5, U^R 5, viscous node flux 4
     static constexpr int NF_INV = 23, NF_VISC = 27;
     __device__ static __forceinline__ int idx(int p, int a) {
         const int s = (p + 4 * RING) & (RING - 1);
-        return DIR == 0 ? a * (RING + 1) + s : s * NA + a;
+        return DIR == 0 ? a * RING + (s ^ ((a & 1) * (RING / 2))) : s * NA + a;
     }
     __device__ static __forceinline__ void split(int it, int X, int& p, int& a) {
         if (DIR == 0) {
@@ -58,8 +61,18 @@ struct FluxLayout {
 // SCH 0: modified AFWENO (characteristic space at the node, Figs. 10-11);
 // SCH 1: original AFWENO (characteristic space at the face from the mean
 // state and the face metric, two independent WENOs per face, Fig. 9).
+// Resident CTAs per SM that the register allocation must allow.  FP64: two
+// of 256 threads (128 registers) or three of 128, so that the FP64 pipe
+// always has a second CTA's warps.  FP32: no target (0); the compiler's own
+// allocation (72-80 registers, three CTAs of 256) measured as fast as a
+// 64-register target and faster than an explicit 85-register one.
+template <class R, int NT>
+constexpr int flux_min_ctas() {
+    return sizeof(R) == 8 ? (NT >= 256 ? 2 : 3) : 0;
+}
+
 template <class R, int DIR, int TP, int NA, bool VISC, bool RK, int SCH>
-__global__ void __launch_bounds__(TP * NA)
+__global__ void __launch_bounds__(TP * NA, flux_min_ctas<R, TP * NA>())
 k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int ntiles,
        const R* __restrict__ Q, const R* __restrict__ met, long long fs, const R* __restrict__ stress,
        R* __restrict__ A, int accumulate, GasR<R> gs, RKArgs rk) {

@@ -26,7 +26,7 @@ FluxShape flux_shape(int dir, int v) {
 size_t flux_smem(bool fp64, int dir, int v, bool visc) {
     const FluxShape sh = flux_shape(dir, v);
     const int ring = sh.tp >= 8 ? 2 * sh.tp : 16;
-    const size_t plane = dir == 0 ? (size_t)sh.na * (ring + 1) : (size_t)ring * sh.na;
+    const size_t plane = (size_t)ring * sh.na;
     return (fp64 ? 8 : 4) * plane * (visc ? 27 : 23);
 }
 

@@ -368,7 +368,7 @@ k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
             stress(gs, prim[e], prim[fs + e], prim[2 * fs + e], prim[3 * fs + e], g, S);
 #pragma unroll
             for (int c = 0; c < 9; ++c) out[c * fs + e] = S[c];
-            push_ghosts<R>(blocks, B, id, out, fs, 9, S, false);   // the stress halo of the sweeps
+            push_ghosts<R>(blocks, B, br.b, id, out, fs, 9, S, false);   // the stress halo of the sweeps
         } else {
 #pragma unroll
             for (int c = 0; c < 12; ++c) out[c * fs + e] = g[c];
