@@ -50,6 +50,17 @@ def flux_bytes_per_node(dir_, word, viscous):
     return words * word
 
 
+def rk_extra_bytes_per_node(precision):
+    """Bytes the fused zeta sweep adds for R = -J A and the RK3 stage: it
+    reads A without writing it (-5 words), and reads Q^n, J and writes
+    Q^(k+1) in FP64.  In the FP64 form the stage input Q^(k) is the stencil
+    state itself; the mixed form reads it in FP64 besides its FP32 copy, and
+    writes the FP32 copy of the output and reads the rest-state residual."""
+    if precision == "fp64":
+        return -5 * 8 + (5 + 1 + 5) * 8
+    return -5 * 4 + (5 + 5 + 1 + 5) * 8 + 5 * 4 + 5 * 4
+
+
 WORKLOADS = {
     "tgv128": ("Taylor-Green vortex, NS Re1600 Ma0.1 Pr0.71, warped periodic 128^3 block", lambda W: W.tgv(128)),
     "tgv256": ("Taylor-Green vortex, NS Re1600 Ma0.1 Pr0.71, warped periodic 256^3 block", lambda W: W.tgv(256)),
@@ -175,7 +186,7 @@ def roofline_for(ctx, w, precision, steps, dt, peaks):
         if name == "flux_zeta_rk":
             # the fused stage reads A instead of read + write, and does the FP64
             # RK3 combination: Q^n, Q^(k), J in, Q^(k+1) out (+ FP32 copy)
-            bytes_ += (-5 * word + 16 * 8 + (5 * 4 if precision == "mixed" else 0)) * npts
+            bytes_ += rk_extra_bytes_per_node(precision) * npts
             flops += RK_FLOPS * npts
         gbs = bytes_ / per_launch_s / 1e9
         tfl = flops / per_launch_s / 1e12

@@ -181,14 +181,13 @@ __device__ __forceinline__ float hmin0(float x) { return fminf(x, 0.0f); }
 
 template <class R>
 struct GasR {   // gas constants in the working precision (built on the host)
-    R gamma, gm1, inv_2gamma, two_gm1, c3g, mach_re, kq_fac, suth, one_p_suth, inv_gm1;
+    R gamma, gm1, inv_2gamma, two_gm1, mach_re, kq_fac, suth, one_p_suth, inv_gm1;
     int mu_law;
     __host__ __device__ void init(const Gas& g) {
         gamma = R(g.gamma);
         gm1 = R(g.gamma - 1.0);
         inv_2gamma = R(1.0 / (2.0 * g.gamma));
         two_gm1 = R(2.0 * (g.gamma - 1.0));
-        c3g = R((3.0 - g.gamma) / (2.0 * (g.gamma - 1.0)));
         mach_re = R(g.mach / g.re);
         kq_fac = R(1.0 / (g.pr * (g.gamma - 1.0)));
         suth = R(g.suth);
@@ -255,8 +254,11 @@ __device__ __forceinline__ R viscosity(const GasR<R>& g, R T) {
 //     e1 = a1 - a2 = w0 - 3w1 + 3w2 - w3, e2 = a2 - a3 (mirrored for the right
 //     value), so left = uL2 + (3 p23 e1 + 5 p12 e2) / (8 dL) and
 //     right = uR2 - (3 p12 e2 + 5 p23 e1) / (8 dR).
-__device__ __forceinline__ void weno_pair(double w0, double w1, double w2, double w3, double w4,
-                                          double& left, double& right) {
+struct WenoParts {   // one field: value = u2 + n / (8 d) for each side
+    double nL, nR, dL, dR, uL2, uR2;
+};
+
+__device__ __forceinline__ WenoParts weno_parts(double w0, double w1, double w2, double w3, double w4) {
     const double eps4 = 4.0e-6;
     const double d10 = w1 - w0, d21 = w2 - w1, d32 = w3 - w2, d43 = w4 - w3;
     const double a1 = d21 - d10, a2 = d32 - d21, a3 = d43 - d32;
@@ -269,17 +271,58 @@ __device__ __forceinline__ void weno_pair(double w0, double w1, double w2, doubl
     s2 *= s2;
     s3 *= s3;
     const double p12 = s1 * s2, p13 = s1 * s3, p23 = s2 * s3;
-    const double dL = fma(10.0, p13, fma(5.0, p12, p23));
-    const double dR = fma(10.0, p13, fma(5.0, p23, p12));
+    WenoParts r;
+    r.dL = fma(10.0, p13, fma(5.0, p12, p23));
+    r.dR = fma(10.0, p13, fma(5.0, p23, p12));
     const double e1 = a1 - a2, e2 = a2 - a3;
     const double A = p23 * e1, B = p12 * e2;
-    const double nL = fma(3.0, A, 5.0 * B), nR = fma(3.0, B, 5.0 * A);
-    const double m2 = 0.75 * w2;
-    const double uL2 = fma(0.375, w3, fma(-0.125, w1, m2));
-    const double uR2 = fma(0.375, w1, fma(-0.125, w3, m2));
-    const double inv = 0.125 / (dL * dR);   // one division for both values
-    left = fma(nL, dR * inv, uL2);
-    right = fma(-nR, dL * inv, uR2);
+    r.nL = fma(3.0, A, 5.0 * B);
+    r.nR = -fma(3.0, B, 5.0 * A);
+    r.uL2 = fma(0.125, fma(3.0, d32, d21), w2);    // (-w1 + 6 w2 + 3 w3) / 8
+    r.uR2 = fma(-0.125, fma(3.0, d21, d32), w2);   // (-w3 + 6 w2 + 3 w1) / 8
+    return r;
+}
+
+__device__ __forceinline__ void weno_pair(double w0, double w1, double w2, double w3, double w4,
+                                          double& left, double& right) {
+    const WenoParts r = weno_parts(w0, w1, w2, w3, w4);
+    const double inv = 0.125 / (r.dL * r.dR);   // one division for both values
+    left = fma(r.nL, r.dR * inv, r.uL2);
+    right = fma(r.nR, r.dL * inv, r.uR2);
+}
+
+// The five characteristic fields of a node with one FP64 division: each
+// field's dL dR is brought to [1, 2) by its binary exponent (integer pipe;
+// dL dR >= 1e-41 from eps), the five reciprocals come from one division of
+// their product and the prefix products, and each is scaled back by its
+// exponent.  W[s][l]: stencil node s = 0..4 (i-2..i+2), field l.
+__device__ __forceinline__ void weno_pair5(const double (&W)[5][5], double (&WL)[5], double (&WR)[5]) {
+    WenoParts r[5];
+    double D[5];
+    int ex[5];
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        r[l] = weno_parts(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l]);
+        const long long b = __double_as_longlong(r[l].dL * r[l].dR);
+        ex[l] = (int)(b >> 52) & 0x7ff;
+        D[l] = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    }
+    const double P1 = D[0] * D[1], P2 = P1 * D[2], P3 = P2 * D[3], P4 = P3 * D[4];
+    double I = 0.125 / P4, inv[5];
+    inv[4] = I * P3;
+    I *= D[4];
+    inv[3] = I * P2;
+    I *= D[3];
+    inv[2] = I * P1;
+    I *= D[2];
+    inv[1] = I * D[0];
+    inv[0] = I * D[1];
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        const double v = __longlong_as_double(__double_as_longlong(inv[l]) - ((long long)(ex[l] - 1023) << 52));
+        WL[l] = fma(r[l].nL, r[l].dR * v, r[l].uL2);
+        WR[l] = fma(r[l].nR, r[l].dL * v, r[l].uR2);
+    }
 }
 
 __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3, float w4, float& left,
@@ -306,6 +349,12 @@ __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3
     const float tR1 = 0.0625f * r3, tR2 = 0.625f * r2, tR3 = 0.3125f * r1;
     left = __fdividef(tL1 * uL1 + tL2 * uL2 + tL3 * uL3, tL1 + tL2 + tL3);
     right = __fdividef(tR1 * uR1 + tR2 * uR2 + tR3 * uR3, tR1 + tR2 + tR3);
+}
+
+// FP32: each field on its own (hardware reciprocals are cheap).
+__device__ __forceinline__ void weno_pair5(const float (&W)[5][5], float (&WL)[5], float (&WR)[5]) {
+#pragma unroll
+    for (int l = 0; l < 5; ++l) weno_pair(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l], WL[l], WR[l]);
 }
 
 // One WENO5 value with its own indicators (original AFWENO, Fig. 9): the
@@ -490,11 +539,32 @@ __device__ __forceinline__ void point_flux(const GasR<R>& gs, const R q[5], R mx
     f[4] = (q[4] + p) * th;
 }
 
+// Positive or negative part of x on the integer pipe (sign-bit mask), so
+// that the split of the eigenvalues costs no floating-point instruction.
+__device__ __forceinline__ double hpos(double x) {
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double(b & ~(b >> 63));
+}
+__device__ __forceinline__ double hneg(double x) {
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double(b & (b >> 63));
+}
+__device__ __forceinline__ float hpos(float x) {
+    const int b = __float_as_int(x);
+    return __int_as_float(b & ~(b >> 31));
+}
+__device__ __forceinline__ float hneg(float x) {
+    const int b = __float_as_int(x);
+    return __int_as_float(b & (b >> 31));
+}
+
 // Steger-Warming split flux along metric (kx, ky, kz) * mm; POS selects F+.
-//   F = rho/(2 gamma) [M, u M + c kx D, v M + c ky D, w M + c kz D,
-//                      (gamma-1) l1 |u|^2 + (l4+l5)(|u|^2+c^2)/2 + c theta D
-//                      + (l4+l5)(3-gamma) c^2 / (2 (gamma-1))]
-//   with l = lambda^+- of (theta, theta + c, theta - c) |m|, M = 2(gamma-1) l1 + l4 + l5, D = l4 - l5.
+//   F = rho |m| / (2 gamma) [M, u M + c kx D, v M + c ky D, w M + c kz D,
+//                            (gamma-1) l1 |u|^2 + (l4+l5) H + c theta D]
+//   with l = lambda^+- of (theta, theta + c, theta - c) (the factor |m| > 0
+//   commutes with the split), M = 2(gamma-1) l1 + l4 + l5, D = l4 - l5 and
+//   H = |u|^2/2 + c^2/(gamma-1): the energy row's (|u|^2+c^2)/2 and
+//   (3-gamma) c^2 / (2 (gamma-1)) terms of (l4+l5) sum to H.
 template <class R, bool POS>
 __device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R kx, R ky, R kz, R mm, R F[5]) {
     const R irho = hrcp(q[0]);
@@ -504,25 +574,26 @@ __device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R kx, R
     const R c2 = gs.gamma * p * irho;
     const R c = c2 * hrsqrt(c2);
     const R th = kx * u + ky * v + kz * w;
-    R l1 = th * mm, l4 = (th + c) * mm, l5 = (th - c) * mm;
+    R l1 = th, l4 = th + c, l5 = th - c;
     if (POS) {
-        l1 = hmax0(l1);
-        l4 = hmax0(l4);
-        l5 = hmax0(l5);
+        l1 = hpos(l1);
+        l4 = hpos(l4);
+        l5 = hpos(l5);
     } else {
-        l1 = hmin0(l1);
-        l4 = hmin0(l4);
-        l5 = hmin0(l5);
+        l1 = hneg(l1);
+        l4 = hneg(l4);
+        l5 = hneg(l5);
     }
-    const R a = q[0] * gs.inv_2gamma;
+    const R a = q[0] * mm * gs.inv_2gamma;
     const R S45 = l4 + l5, D45 = l4 - l5;
-    const R M = gs.two_gm1 * l1 + S45;
-    const R cD = c * D45;
-    F[0] = a * M;
-    F[1] = a * (u * M + kx * cD);
-    F[2] = a * (v * M + ky * cD);
-    F[3] = a * (w * M + kz * cD);
-    F[4] = a * (gs.gm1 * l1 * uu + R(0.5) * S45 * (uu + c2) + th * cD + S45 * c2 * gs.c3g);
+    const R aM = a * (gs.two_gm1 * l1 + S45);
+    const R acD = a * (c * D45);
+    const R H = R(0.5) * uu + c2 * gs.inv_gm1;
+    F[0] = aM;
+    F[1] = u * aM + kx * acD;
+    F[2] = v * aM + ky * acD;
+    F[3] = w * aM + kz * acD;
+    F[4] = a * (gs.gm1 * l1 * uu + S45 * H) + th * acD;
 }
 
 // Stress tensor and work + heat-flux vector at a node, Eqs. (5)-(6) and the

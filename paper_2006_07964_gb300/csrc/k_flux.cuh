@@ -163,8 +163,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         cb.project(sQ[si], sQ[PL + si], sQ[2 * PL + si], sQ[3 * PL + si], sQ[4 * PL + si], W[s + 2]);
                     }
                     R WL[5], WR[5];
-#pragma unroll
-                    for (int l = 0; l < 5; ++l) weno_pair(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l], WL[l], WR[l]);
+                    weno_pair5(W, WL, WR);
                     R U[5];
                     cb.back(WL, U);
 #pragma unroll
