@@ -38,6 +38,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # once per node by the gradient kernel).
 FLUX_FLOPS_INV = 1060
 FLUX_FLOPS_VISC = 50
+# The FP64 form reads the sweeps' unit normals, formed once from the static
+# metrics: per node and direction the sixth-order midpoint face metric
+# (3 x 9), its norm, square root and normalisation (10) and the node
+# normal's norm and normalisation (9) are not part of a stage.
+FLUX_FLOPS_STATIC_FP64 = 46
+NRM_WORDS_FP64 = 7   # node normal (3), face normal (3), face |m| (1) per node and direction
 RK_FLOPS = 30   # R = -J A and the three-term combination, five components
 
 
@@ -183,6 +189,9 @@ def roofline_for(ctx, w, precision, steps, dt, peaks):
         word = 8 if precision == "fp64" else 4
         flops = (FLUX_FLOPS_INV + (FLUX_FLOPS_VISC if w.viscous else 0)) * npts
         bytes_ = flux_bytes_per_node(d, word, w.viscous) * npts
+        if precision == "fp64":
+            flops -= FLUX_FLOPS_STATIC_FP64 * npts
+            bytes_ += NRM_WORDS_FP64 * 8 * npts
         if name == "flux_zeta_rk":
             # the fused stage reads A instead of read + write, and does the FP64
             # RK3 combination: Q^n, Q^(k), J in, Q^(k+1) out (+ FP32 copy)

@@ -407,7 +407,8 @@ template <class R>
 struct CharBasis {
     R kx, ky, kz, u, v, w, rho, irho, p, c, a0, g, gu, gv, gw, cir, kxi, kyi, kzi, kxs, kys, kzs, al, alc, acth,
         half_uu, H;
-    __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
+    // the state part (the node flux needs only this) ...
+    __device__ __forceinline__ void init_state(const GasR<R>& gs, const R q[5]) {
         irho = hrcp(q[0]);
         rho = q[0];
         u = q[1] * irho;
@@ -418,10 +419,6 @@ struct CharBasis {
         const R c2 = gs.gamma * p * irho;
         const R ic = hrsqrt(c2);
         c = c2 * ic;
-        const R imm = hrsqrt(mx * mx + my * my + mz * mz);
-        kx = mx * imm;
-        ky = my * imm;
-        kz = mz * imm;
         const R phi2 = gs.gm1 * half_uu;
         const R ic2 = ic * ic;
         a0 = R(1) - phi2 * ic2;
@@ -429,19 +426,29 @@ struct CharBasis {
         gu = g * u;
         gv = g * v;
         gw = g * w;
-        // the projection works on rho d = (Q_m - u_m Q_0); 1/rho and 1/sqrt(2)
-        // go into the normal once per node
+        cir = c * irho * R(0.70710678118654752440);
+        al = rho * ic * R(0.70710678118654752440);
+        alc = al * c;
+        H = half_uu + c2 * gs.inv_gm1;
+    }
+    // ... and the unit normal k.  The projection works on rho d = (Q_m - u_m
+    // Q_0); 1/rho and 1/sqrt(2) go into the normal once per node.
+    __device__ __forceinline__ void set_normal(R kx_, R ky_, R kz_) {
+        kx = kx_;
+        ky = ky_;
+        kz = kz_;
         kxi = kx * irho;
         kyi = ky * irho;
         kzi = kz * irho;
         kxs = kxi * R(0.70710678118654752440);
         kys = kyi * R(0.70710678118654752440);
         kzs = kzi * R(0.70710678118654752440);
-        cir = c * irho * R(0.70710678118654752440);
-        al = rho * ic * R(0.70710678118654752440);
-        alc = al * c;
-        H = half_uu + c2 * gs.inv_gm1;
         acth = alc * (kx * u + ky * v + kz * w);
+    }
+    __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
+        init_state(gs, q);
+        const R imm = hrsqrt(mx * mx + my * my + mz * mz);
+        set_normal(mx * imm, my * imm, mz * imm);
     }
     // W = L q
     __device__ __forceinline__ void project(R q0, R q1, R q2, R q3, R q4, R W[5]) const {
@@ -475,7 +482,7 @@ template <>
 struct CharBasis<float> {
     using R = float;
     R kx, ky, kz, u, v, w, rho, irho, p, c, a0, g, cir, al, half_uu, H, cth;
-    __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
+    __device__ __forceinline__ void init_state(const GasR<R>& gs, const R q[5]) {
         irho = hrcp(q[0]);
         rho = q[0];
         u = q[1] * irho;
@@ -486,10 +493,6 @@ struct CharBasis<float> {
         const R c2 = gs.gamma * p * irho;
         const R ic = hrsqrt(c2);
         c = c2 * ic;
-        const R imm = hrsqrt(mx * mx + my * my + mz * mz);
-        kx = mx * imm;
-        ky = my * imm;
-        kz = mz * imm;
         const R phi2 = gs.gm1 * half_uu;
         const R ic2 = ic * ic;
         a0 = R(1) - phi2 * ic2;
@@ -497,7 +500,17 @@ struct CharBasis<float> {
         cir = c * irho * R(0.70710678118654752440);
         al = rho * ic * R(0.70710678118654752440);
         H = half_uu + c2 * gs.inv_gm1;
+    }
+    __device__ __forceinline__ void set_normal(R kx_, R ky_, R kz_) {
+        kx = kx_;
+        ky = ky_;
+        kz = kz_;
         cth = c * (kx * u + ky * v + kz * w);
+    }
+    __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
+        init_state(gs, q);
+        const R imm = hrsqrt(mx * mx + my * my + mz * mz);
+        set_normal(mx * imm, my * imm, mz * imm);
     }
     // W = L q
     __device__ __forceinline__ void project(R q0, R q1, R q2, R q3, R q4, R W[5]) const {

@@ -34,8 +34,9 @@ struct FluxLayout {
     // half-warps fall on complementary banks.  DIR 1, 2: lanes run across
     // (i), planes [slot][line].
     static constexpr int PLANE = RING * NA;
-    // fields per ring slot: Q 5, metric 3, node flux 5, U^L (then h) 5, U^R 5, viscous node flux 4
-    static constexpr int NF_INV = 23, NF_VISC = 27;
+    // fields per ring slot: Q 5, metric 3, node flux 5, U^L (then h) 5, U^R 5, viscous node flux 4;
+    // FP64 adds the stored unit normals of the node (3) and of its + face (4)
+    static constexpr int NF_INV = 23, NF_VISC = 27, NF_NRM = 7;
     __device__ static __forceinline__ int idx(int p, int a) {
         const int s = (p + 4 * RING) & (RING - 1);
         return DIR == 0 ? a * RING + (s ^ ((a & 1) * (RING / 2))) : s * NA + a;
@@ -51,7 +52,7 @@ struct FluxLayout {
     }
     template <class R, bool VISC>
     static constexpr size_t smem_bytes() {
-        return sizeof(R) * (size_t)PLANE * (VISC ? NF_VISC : NF_INV);
+        return sizeof(R) * (size_t)PLANE * ((VISC ? NF_VISC : NF_INV) + (sizeof(R) == 8 ? NF_NRM : 0));
     }
 };
 
@@ -74,8 +75,8 @@ constexpr int flux_min_ctas() {
 template <class R, int DIR, int TP, int NA, bool VISC, bool RK, int SCH>
 __global__ void __launch_bounds__(TP * NA, flux_min_ctas<R, TP * NA>())
 k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int ntiles,
-       const R* __restrict__ Q, const R* __restrict__ met, long long fs, const R* __restrict__ stress,
-       R* __restrict__ A, int accumulate, GasR<R> gs, RKArgs rk) {
+       const R* __restrict__ Q, const R* __restrict__ met, const R* __restrict__ nrm, long long fs,
+       const R* __restrict__ stress, R* __restrict__ A, int accumulate, GasR<R> gs, RKArgs rk) {
     using LY = FluxLayout<DIR, TP, NA>;
     constexpr int PL = LY::PLANE;
     constexpr int NT = TP * NA;
@@ -86,6 +87,11 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
     R* sUL = sF + 5 * PL;                      // 5 (U^L at the + face, then h)
     R* sUR = sUL + 5 * PL;                     // 5 (U^R at the - face)
     R* sFv = sUR + 5 * PL;                     // 4 (VISC)
+    R* sKn = sFv + (VISC ? 4 : 0) * PL;        // 3 (FP64): node unit normal
+    R* sKf = sKn + 3 * PL;                     // 4 (FP64): + face unit normal and |m|
+    // FP64 with stored normals (static grid data, k_normals): the node basis
+    // and the face metric are read instead of formed from the metric
+    const bool pre = sizeof(R) == 8 && nrm != nullptr;
     const int tid = threadIdx.x;
 
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -115,6 +121,15 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     for (int f = 0; f < 5; ++f) sQ[f * PL + s] = Q[f * fs + e];
 #pragma unroll
                     for (int f = 0; f < 3; ++f) sM[f * PL + s] = met[(3 * DIR + f) * fs + e];
+                    if (pre && p >= -1 && p <= n) {
+                        const R* nr = nrm + 7 * DIR * fs + e;
+#pragma unroll
+                        for (int f = 0; f < 3; ++f) sKn[f * PL + s] = nr[f * fs];
+                        if (p <= n - 1) {
+#pragma unroll
+                            for (int f = 0; f < 4; ++f) sKf[f * PL + s] = nr[(3 + f) * fs];
+                        }
+                    }
                 }
             }
             __syncthreads();
@@ -139,7 +154,10 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     for (int f = 0; f < 5; ++f) q[f] = sQ[f * PL + s0];
                     const R mx = sM[s0], my = sM[PL + s0], mz = sM[2 * PL + s0];
                     CharBasis<R> cb;
-                    cb.init(gs, q, mx, my, mz);
+                    if (pre)
+                        cb.init_state(gs, q);
+                    else
+                        cb.init(gs, q, mx, my, mz);
                     // node flux along the un-normalised metric, Eq. (4)
                     {
                         const R th = mx * cb.u + my * cb.v + mz * cb.w;
@@ -156,6 +174,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         sFv[3 * PL + s0] = mx * S[6] + my * S[7] + mz * S[8];
                     }
                     if (SCH == 1 || p < -1 || p > n) continue;   // WENO only where a face needs it
+                    if (pre) cb.set_normal(sKn[s0], sKn[PL + s0], sKn[2 * PL + s0]);
                     R W[5][5];
 #pragma unroll
                     for (int s = -2; s <= 2; ++s) {
@@ -182,18 +201,28 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     LY::split(it, cnt, f, a);
                     f += first;
                     if (a0 + a >= na || f > n - 1) continue;
-                    R mf[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const R* m = sM + k * PL;
-                        mf[k] = mid6<R>(m[LY::idx(f - 2, a)], m[LY::idx(f - 1, a)], m[LY::idx(f, a)],
-                                        m[LY::idx(f + 1, a)], m[LY::idx(f + 2, a)], m[LY::idx(f + 3, a)]);
-                    }
-                    const R mm2 = mf[0] * mf[0] + mf[1] * mf[1] + mf[2] * mf[2];
-                    const R imm = hrsqrt(mm2);
-                    const R mm = mm2 * imm;
-                    const R kx = mf[0] * imm, ky = mf[1] * imm, kz = mf[2] * imm;
                     const int uf = LY::idx(f, a), ur = LY::idx(f + 1, a);
+                    R kx, ky, kz, mm;
+                    if (pre) {
+                        kx = sKf[uf];
+                        ky = sKf[PL + uf];
+                        kz = sKf[2 * PL + uf];
+                        mm = sKf[3 * PL + uf];
+                    } else {
+                        R mf[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const R* m = sM + k * PL;
+                            mf[k] = mid6<R>(m[LY::idx(f - 2, a)], m[LY::idx(f - 1, a)], m[LY::idx(f, a)],
+                                            m[LY::idx(f + 1, a)], m[LY::idx(f + 2, a)], m[LY::idx(f + 3, a)]);
+                        }
+                        const R mm2 = mf[0] * mf[0] + mf[1] * mf[1] + mf[2] * mf[2];
+                        const R imm = hrsqrt(mm2);
+                        mm = mm2 * imm;
+                        kx = mf[0] * imm;
+                        ky = mf[1] * imm;
+                        kz = mf[2] * imm;
+                    }
                     R ql[5], qr[5], Fp[5], Fm[5];
                     if (SCH == 0) {
 #pragma unroll
@@ -206,7 +235,8 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
 #pragma unroll
                         for (int k = 0; k < 5; ++k) qm[k] = R(0.5) * (sQ[k * PL + uf] + sQ[k * PL + ur]);
                         CharBasis<R> cb;
-                        cb.init(gs, qm, mf[0], mf[1], mf[2]);
+                        cb.init_state(gs, qm);
+                        cb.set_normal(kx, ky, kz);
                         R W[6][5];
 #pragma unroll
                         for (int s = -2; s <= 3; ++s) {

@@ -27,7 +27,7 @@ size_t flux_smem(bool fp64, int dir, int v, bool visc) {
     const FluxShape sh = flux_shape(dir, v);
     const int ring = sh.tp >= 8 ? 2 * sh.tp : 16;
     const size_t plane = (size_t)ring * sh.na;
-    return (fp64 ? 8 : 4) * plane * (visc ? 27 : 23);
+    return (fp64 ? 8 : 4) * plane * ((visc ? 27 : 23) + (fp64 ? 7 : 0));
 }
 
 int flux_ctas_per_sm(bool fp64, int dir, int v, bool visc, bool rk, int scheme) {

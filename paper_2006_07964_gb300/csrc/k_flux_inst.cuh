@@ -38,8 +38,8 @@ struct FluxInst {
         GasR<R> gs;
         gs.init(a.gas);
         k_flux<R, DIR, TP, NA, VISC, RK, SCH><<<a.grid, TP * NA, smem, s>>>(
-            a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, a.fs, (const R*)a.stress, (R*)a.A,
-            a.accumulate, gs, a.rk);
+            a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, (const R*)a.nrm, a.fs,
+            (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
         return cudaGetLastError();
     }
 };

@@ -303,6 +303,58 @@ k_metrics(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__
     }
 }
 
+// Unit normals of the sweeps (FP64 form; static grid data, formed once).
+// For each direction d, on the lines of the interior: the node normal
+// m_d/|m_d| at nodes -1..n (the nodes whose characteristic basis a sweep
+// forms) and, for faces -1/2 .. n-1/2 (stored at the node below), the unit
+// normal and norm of the sixth-order midpoint metric.  Fields 7d + 0..2:
+// node normal; 7d + 3..5: face normal; 7d + 6: face |m|.  The formulas are
+// the sweep kernel's own.
+__global__ void __launch_bounds__(kThreads)
+k_normals(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks,
+          const double* __restrict__ met, long long fs, double* __restrict__ nrm) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const DevBlock& B = blocks[br.b];
+        const int id[3] = {i, j, k};
+        const long long e = node_index(B, i, j, k);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            bool line = id[d] >= -1 && id[d] <= B.n[d];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (a != d && (id[a] < 0 || id[a] >= B.n[a])) line = false;
+            if (!line) continue;
+            const long long st = d == 0 ? 1 : (d == 1 ? B.sj : B.sk);
+            const double* m = met + 3 * d * fs + e;
+            const double mx = m[0], my = m[fs], mz = m[2 * fs];
+            const double imm = hrsqrt(mx * mx + my * my + mz * mz);
+            double* o = nrm + 7 * d * fs + e;
+            o[0] = mx * imm;
+            o[fs] = my * imm;
+            o[2 * fs] = mz * imm;
+            if (id[d] <= B.n[d] - 1) {
+                double mf[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double* q = m + c * fs;
+                    mf[c] = mid6<double>(q[-2 * st], q[-st], q[0], q[st], q[2 * st], q[3 * st]);
+                }
+                const double mm2 = mf[0] * mf[0] + mf[1] * mf[1] + mf[2] * mf[2];
+                const double im = hrsqrt(mm2);
+                o[3 * fs] = mf[0] * im;
+                o[4 * fs] = mf[1] * im;
+                o[5 * fs] = mf[2] * im;
+                o[6 * fs] = mm2 * im;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- primitives
 template <class R>
 __global__ void __launch_bounds__(kThreads)
@@ -576,6 +628,13 @@ cudaError_t launch_metrics(const Brick* bricks, int nb, const DevBlock* cblocks,
     if (nb <= 0) return cudaSuccess;
     k_metrics<<<grid_for((long long)nb * kThreads), kThreads, 0, s>>>(bricks, nb, cblocks, X, fsc, blocks, met, fs,
                                                                       flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normals(const Brick* bricks, int nb, const DevBlock* blocks, const double* met, long long fs,
+                           double* nrm, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    k_normals<<<grid_for((long long)nb * kThreads), kThreads, 0, s>>>(bricks, nb, blocks, met, fs, nrm);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ struct FluxArgs {
     long long fs;       // field stride (elements)
     const void* stress; // R, 9 fields (tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, beta), Navier-Stokes only
     void* A;            // R, 5 fields, accumulated divergence
+    const void* nrm;    // FP64 form: the sweep normals (k_normals, 21 fields), or null
     int accumulate;
     Gas gas;
     int grid;           // CTAs of the persistent launch
@@ -51,6 +52,8 @@ cudaError_t launch_halo_coords(const HaloItem* items, int n, double* X, long lon
 cudaError_t launch_metrics(const Brick* bricks, int nb, const DevBlock* cblocks, const double* X, long long fsc,
                            const DevBlock* blocks, double* met, long long fs, unsigned* flags, cudaStream_t s);
 cudaError_t launch_cast(const double* src, float* dst, long long n, cudaStream_t s);
+cudaError_t launch_normals(const Brick* bricks, int nb, const DevBlock* blocks, const double* met, long long fs,
+                           double* nrm, cudaStream_t s);
 cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, const void* Q, bool fp64,
                         long long fs, void* prim, Gas gas, cudaStream_t s);
 // Gradients (u,v,w,T)_(x,y,z) (12 fields, stress_mode = false) or the node

@@ -63,6 +63,7 @@ struct hx_ctx {
     std::vector<void*> allocs;
 
     double *met = nullptr, *Qn = nullptr, *Qa = nullptr, *Qb = nullptr, *stage = nullptr;
+    double* nrm = nullptr;     // FP64 form: unit normals of the sweeps (k_normals), 21 fields
     float *metf = nullptr;
     float* Aref = nullptr;   // mixed form: FP32 divergence of the rest state (pure rounding)
     float* Qf[3] = {nullptr, nullptr, nullptr};   // mixed form: FP32 copies of Qn, Qa, Qb
@@ -289,6 +290,7 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
         a.ntiles = ctx->ntiles[d][v];
         a.Q = Qs;
         a.met = M;
+        a.nrm = ctx->nrm;
         a.fs = ctx->fs;
         a.stress = ctx->grad;
         a.A = ctx->A;
@@ -394,6 +396,7 @@ int autotune(hx_ctx* ctx) {
                 a.ntiles = ctx->ntiles[d][v];
                 a.Q = stencil_state(ctx, 0);
                 a.met = stencil_met(ctx);
+                a.nrm = ctx->nrm;
                 a.fs = ctx->fs;
                 a.stress = ctx->grad;
                 a.A = ctx->A;
@@ -762,7 +765,10 @@ int hx_finalize(hx_ctx* ctx) {
         if ((rc = dalloc(ctx, &ctx->prim, 4 * fs * r))) return rc;
         if ((rc = dalloc(ctx, &ctx->grad, 12 * fs * r))) return rc;
     }
-    if (!ctx->fp64()) {
+    if (ctx->fp64()) {
+        if ((rc = dalloc(ctx, (void**)&ctx->nrm, 21 * fs * 8))) return rc;
+        HX_CK(launch_fill(ctx->nrm, true, 21 * ctx->fs, 0.0, ctx->stream));
+    } else {
         for (int q = 0; q < 3; ++q)
             if ((rc = dalloc(ctx, (void**)&ctx->Qf[q], 5 * fs * 4))) return rc;
         if ((rc = dalloc(ctx, (void**)&ctx->metf, 10 * fs * 4))) return rc;
@@ -896,7 +902,10 @@ int hx_compute_metrics(hx_ctx* ctx) {
     HX_CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned), ctx->stream));
     HX_CK(launch_metrics(dbm, (int)bm.size(), dc, X, ctx->fsc, ctx->d_blocks, ctx->met, ctx->fs, ctx->d_flags,
                          ctx->stream));
-    if (!ctx->fp64()) HX_CK(launch_cast(ctx->met, ctx->metf, 10 * ctx->fs, ctx->stream));
+    if (ctx->fp64())
+        HX_CK(launch_normals(dbm, (int)bm.size(), ctx->d_blocks, ctx->met, ctx->fs, ctx->nrm, ctx->stream));
+    else
+        HX_CK(launch_cast(ctx->met, ctx->metf, 10 * ctx->fs, ctx->stream));
     unsigned flags = 0;
     HX_CK(cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream));
     HX_CK(cudaStreamSynchronize(ctx->stream));
