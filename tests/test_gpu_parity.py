@@ -278,6 +278,28 @@ def test_mixed_precision_rhs_close():
     assert rel_linf(ctx.rhs(0), P.get_rhs(0), "rhs") < 1e-4
 
 
+@pytest.mark.parametrize("name", ["tgv24", "ragged_ns", "split_ns", "rotated_ns", "ogrid_s8"])
+def test_mixed_precision_ns_rhs_close(name):
+    """Mixed-form Navier-Stokes residual (FP32 node stress, viscous and
+    inviscid fluxes) against the FP64 oracle on ragged blocks (partial
+    stress tiles), interfaces (stress pushed across, also between rotated
+    blocks) and the O-grid's wall and far-field faces.  FP32 rounds the O(1)
+    fluxes whose differences form R, so the error is measured against that
+    scale, max|Q| max_nodes(J sum_d |m_d|), not against R itself (at Mach
+    0.1 R is 1e-3 of it): within 1e-5 of it, about 170 FP32 roundings."""
+    w = CASES[name]()
+    ctx = hx.from_workload(w, precision="mixed")
+    P = oracle.from_workload(w)
+    P.rhs()
+    for b in range(len(w.blocks)):
+        m = P.get_metrics(b)
+        inv_h = (m[9] * (np.sqrt((m[0:3] ** 2).sum(0)) + np.sqrt((m[3:6] ** 2).sum(0)) +
+                         np.sqrt((m[6:9] ** 2).sum(0)))).max()
+        scale = np.abs(w.blocks[b].q0).max() * inv_h
+        err = np.abs(ctx.rhs(b) - P.get_rhs(b)).max()
+        assert err < 1e-5 * scale, (name, b, err, scale)
+
+
 # ---------------------------------------------------------------- error paths
 
 def test_error_topology():
