@@ -47,6 +47,17 @@ NRM_WORDS_FP64 = 7   # node normal (3), face normal (3), face |m| (1) per node a
 RK_FLOPS = 30   # R = -J A and the three-term combination, five components
 
 
+# DRAM bytes (read + write) of one launch of each sweep on the Taylor-Green
+# 128^3 workload, from one ncu capture of the current kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/flux_fp64_tgv128.md
+# and profiles/flux_mixed_tgv128.md give the command).  Another workload, or a
+# kernel changed since the capture, reports null.
+TRAFFIC_TGV128 = {
+    ("fp64", "flux_xi"): 528.3e6, ("fp64", "flux_eta"): 639.7e6, ("fp64", "flux_zeta_rk"): 761.3e6,
+    ("mixed", "flux_xi"): 193.3e6, ("mixed", "flux_eta"): 241.4e6, ("mixed", "flux_zeta_rk"): 580.1e6,
+}
+
+
 def flux_bytes_per_node(dir_, word, viscous):
     """Compulsory HBM bytes per node of one flux-sweep launch: the state (5),
     the metric of the direction (3), the accumulator (written by the xi sweep,
@@ -162,10 +173,10 @@ def pinned_like(torch, a):
     return t
 
 
-def run_form(torch, hx, w, precision, steps, warmup, stream, dt):
+def run_form(torch, hx, w, precision, steps, warmup, stream, dt, autotune=1):
     """Times `steps` graph-replayed RK3 steps with CUDA events on the
     context's stream; returns (seconds, ctx)."""
-    ctx = hx.from_workload(w, precision=precision, stream=stream.cuda_stream)
+    ctx = hx.from_workload(w, precision=precision, stream=stream.cuda_stream, autotune=autotune)
     ctx.step(warmup, dt)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -211,7 +222,9 @@ def roofline_for(ctx, w, precision, steps, dt, peaks):
             out.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
                         "peak_src": peaks["src"],
                         "alu_view": {"achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac}})
-    out["traffic"] = None
+    out["traffic"] = TRAFFIC_TGV128.get((precision, name)) if w.name == "tgv128" else None
+    if out["traffic"] is not None:
+        out["traffic_src"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/)"
     out["per_kernel_ms"] = {k: v[1] / v[0] for k, v in stats.items()}
     out["autotune"] = ctx.tuning()
     return out
@@ -376,6 +389,8 @@ def main():
     ap.add_argument("--workload", default="tgv128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed 128-thread tiles instead of timing the candidates (reproducible profiles)")
     ap.add_argument("--forms", default="fp64,mixed", help="comma list of fp64, mixed")
     ap.add_argument("--report", choices=["precision", "batch", "scheme"], default=None,
                     help="print a precision (mixed vs FP64 errors) or batch (batched vs per-instance) report "
@@ -455,7 +470,8 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    secs, ctx = run_form(torch, hx, w, head, args.steps, args.warmup, stream, dt)
+    tune = 0 if args.no_autotune else 1
+    secs, ctx = run_form(torch, hx, w, head, args.steps, args.warmup, stream, dt, tune)
     ck = clocks.stop()
     barrier()
     secs = max_over_ranks(secs)
@@ -466,7 +482,7 @@ def main():
 
     mixed = None
     if head == "fp64" and "mixed" in forms:
-        msecs, mctx = run_form(torch, hx, w, "mixed", args.steps, args.warmup, stream, dt)
+        msecs, mctx = run_form(torch, hx, w, "mixed", args.steps, args.warmup, stream, dt, tune)
         msecs = max_over_ranks(msecs)
         mval = ranks.throughput(w.npts, args.steps, msecs)
         mixed = {"value": mval, "ms_per_step": msecs / args.steps * 1e3, "ratio_vs_fp64": mval / value,
@@ -476,7 +492,7 @@ def main():
 
     # end to end through the C ABI with host (pinned) buffers: per step the
     # state goes host -> device, one RK3 step runs, the state comes back
-    ectx = hx.from_workload(w, precision=head, stream=stream.cuda_stream)
+    ectx = hx.from_workload(w, precision=head, stream=stream.cuda_stream, autotune=tune)
     hq = [pinned_like(torch, b.q0) for b in w.blocks]
     hout = [torch.empty(b.q0.shape, dtype=torch.float64).pin_memory() for b in w.blocks]
     h2d = sum(b.q0.nbytes for b in w.blocks)

@@ -81,7 +81,10 @@ typedef struct {
                              (characteristic space at the face, two WENOs per face,
                              Fig. 9), kept to measure the modification              */
     size_t mem_cap_bytes; /* 0: no cap; else hx_finalize fails with HX_ERR_OOM above it */
-    int autotune;         /* 1: time the tile-shape candidates once per shape class     */
+    int autotune;         /* 1: time the tile-shape candidates once per shape class
+                             (process-wide cache); 0: take the 128-thread tiles
+                             (16 x 8 along xi, 8 x 16 across), reproducible for
+                             profiling                                               */
 } hx_config;
 
 typedef struct hx_ctx hx_ctx;

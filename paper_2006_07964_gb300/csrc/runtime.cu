@@ -420,9 +420,10 @@ int autotune(hx_ctx* ctx) {
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-        } else {
-            for (int v = 0; v < kFluxVariants && best < 0; ++v)
-                if (flux_ctas_per_sm(f64, d, v, visc, false, ctx->cfg.scheme) > 0) best = v;
+        } else {   // the 128-thread tile (16 x 8 along xi, 8 x 16 across), else the first that launches
+            const int order[kFluxVariants] = {2, 0, 1};
+            for (int o = 0; o < kFluxVariants && best < 0; ++o)
+                if (flux_ctas_per_sm(f64, d, order[o], visc, false, ctx->cfg.scheme) > 0) best = order[o];
         }
         if (best < 0) return fail(ctx, HX_ERR_CUDA, "no flux kernel variant can launch on this device");
         ctx->variant[d] = best;
