@@ -325,30 +325,32 @@ __device__ __forceinline__ void weno_pair5(const double (&W)[5][5], double (&WL)
     }
 }
 
+// FP32: the same algebra as the FP64 form with one hardware reciprocal per
+// side (dL, dR >= 4e-21 from eps, and below FP32's range limit for
+// indicators up to about 4e9, far beyond any physical state in these units).
 __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3, float w4, float& left,
                                           float& right) {
-    const float eps = 1.0e-6f;
-    const float a1 = w0 - 2.0f * w1 + w2, c1 = w0 - 4.0f * w1 + 3.0f * w2;
-    const float a2 = w1 - 2.0f * w2 + w3, c2 = w1 - w3;
-    const float a3 = w2 - 2.0f * w3 + w4, c3 = 3.0f * w2 - 4.0f * w3 + w4;
-    const float b1 = (13.0f / 12.0f) * a1 * a1 + 0.25f * c1 * c1;
-    const float b2 = (13.0f / 12.0f) * a2 * a2 + 0.25f * c2 * c2;
-    const float b3 = (13.0f / 12.0f) * a3 * a3 + 0.25f * c3 * c3;
-    // reciprocal form: no overflow of products of squared indicators in FP32
-    float r1 = __fdividef(1.0f, eps + b1), r2 = __fdividef(1.0f, eps + b2), r3 = __fdividef(1.0f, eps + b3);
-    r1 *= r1;
-    r2 *= r2;
-    r3 *= r3;
-    const float uL1 = 0.375f * w0 - 1.25f * w1 + 1.875f * w2;
-    const float uL2 = -0.125f * w1 + 0.75f * w2 + 0.375f * w3;
-    const float uL3 = 0.375f * w2 + 0.75f * w3 - 0.125f * w4;
-    const float uR1 = 0.375f * w4 - 1.25f * w3 + 1.875f * w2;
-    const float uR2 = -0.125f * w3 + 0.75f * w2 + 0.375f * w1;
-    const float uR3 = 0.375f * w2 + 0.75f * w1 - 0.125f * w0;
-    const float tL1 = 0.0625f * r1, tL2 = 0.625f * r2, tL3 = 0.3125f * r3;
-    const float tR1 = 0.0625f * r3, tR2 = 0.625f * r2, tR3 = 0.3125f * r1;
-    left = __fdividef(tL1 * uL1 + tL2 * uL2 + tL3 * uL3, tL1 + tL2 + tL3);
-    right = __fdividef(tR1 * uR1 + tR2 * uR2 + tR3 * uR3, tR1 + tR2 + tR3);
+    const float eps4 = 4.0e-6f;
+    const float d10 = w1 - w0, d21 = w2 - w1, d32 = w3 - w2, d43 = w4 - w3;
+    const float a1 = d21 - d10, a2 = d32 - d21, a3 = d43 - d32;
+    const float c1 = fmaf(2.0f, d21, a1), c2 = d21 + d32, c3 = fmaf(-2.0f, d32, a3);
+    const float k = 13.0f / 3.0f;
+    float s1 = fmaf(a1, k * a1, fmaf(c1, c1, eps4));
+    float s2 = fmaf(a2, k * a2, fmaf(c2, c2, eps4));
+    float s3 = fmaf(a3, k * a3, fmaf(c3, c3, eps4));
+    s1 *= s1;
+    s2 *= s2;
+    s3 *= s3;
+    const float p12 = s1 * s2, p13 = s1 * s3, p23 = s2 * s3;
+    const float t13 = 10.0f * p13;
+    const float dL = fmaf(5.0f, p12, p23) + t13, dR = fmaf(5.0f, p23, p12) + t13;
+    const float e1 = a1 - a2, e2 = a2 - a3;
+    const float A = p23 * e1, B = p12 * e2;
+    const float nL = fmaf(3.0f, A, 5.0f * B), nR = fmaf(3.0f, B, 5.0f * A);
+    const float uL2 = fmaf(0.125f, fmaf(3.0f, d32, d21), w2);
+    const float uR2 = fmaf(-0.125f, fmaf(3.0f, d21, d32), w2);
+    left = fmaf(nL, __fdividef(0.125f, dL), uL2);
+    right = fmaf(-nR, __fdividef(0.125f, dR), uR2);
 }
 
 // FP32: each field on its own (hardware reciprocals are cheap).
