@@ -300,6 +300,31 @@ def test_mixed_precision_ns_rhs_close(name):
         assert err < 1e-5 * scale, (name, b, err, scale)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["vortex32", "ragged_ns", "rotated_ns", "ogrid_s8"])
+def test_repeated_runs_are_bitwise_identical(name, precision):
+    """Race check without a sanitizer: the residual evaluated three times,
+    and two steps taken twice from the same state, agree bit for bit.  A race
+    on the shared-memory ring of the sweeps, on the halo pushes or on the
+    stage buffers would show up as run-to-run differences."""
+    w = CASES[name]()
+    ctx = hx.from_workload(w, precision=precision)
+    nb = len(w.blocks)
+    r0 = [ctx.rhs(b) for b in range(nb)]
+    for _ in range(2):
+        for b in range(nb):
+            assert np.array_equal(ctx.rhs(b), r0[b]), (name, b)
+    dt, _ = ctx.compute_dt(0.5)
+    q0 = [ctx.get_state(b) for b in range(nb)]
+    ctx.step(2, dt)
+    q1 = [ctx.get_state(b) for b in range(nb)]
+    for b in range(nb):
+        ctx.set_state(b, q0[b])
+    ctx.step(2, dt)
+    for b in range(nb):
+        assert np.array_equal(ctx.get_state(b), q1[b]), (name, b)
+
+
 # ---------------------------------------------------------------- error paths
 
 def test_error_topology():
