@@ -183,6 +183,45 @@ def test_full_size_tgv128_two_steps():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("n", [256, 384])
+def test_full_size_tgv_large_one_step(n):
+    """The precision report's Taylor-Green sizes (16,777,216 and 56,623,104
+    nodes): one FP64 RK3 step against the oracle on every node, then the
+    mixed form's step within its FP32 bound (rel. L2 per variable)."""
+    w = W.tgv(n)
+    P = oracle.from_workload(w)
+    dt, _ = P.dt(0.5)
+    P.step(1, dt)
+    ref = P.get_state(0)
+    del P
+    ctx = hx.from_workload(w)
+    ctx.step(1, dt)
+    assert rel_linf(ctx.get_state(0), ref) < TOL
+    ctx.close()
+    m = hx.from_workload(w, precision="mixed")
+    m.step(1, dt)
+    a = m.get_state(0)
+    m.close()
+    for v in (0, 1, 4):
+        assert np.linalg.norm(a[v] - ref[v]) / np.linalg.norm(ref[v]) < 1e-6, v
+
+
+@pytest.mark.slow
+def test_full_size_batch64_two_steps():
+    """The batched workload at full size: 64 uneven vortex instances
+    (10,634,752 nodes), per-instance dt, two RK3 steps, every node of every
+    instance."""
+    w = W.batch()
+    ctx = hx.from_workload(w)
+    P = oracle.from_workload(w)
+    _, per = P.dt(0.5)
+    ctx.step(2, per)
+    P.step(2, per)
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.get_state(b), P.get_state(b)) < TOL, b
+
+
+@pytest.mark.slow
 def test_full_size_ogrid_residual_and_step():
     """The 8-block O-grid at full size (3,538,944 nodes): residual of every
     block, then one RK3 step."""
