@@ -66,6 +66,8 @@ def load():
         "orc_step": (None, [VP, I, D]),
         "orc_step_multi": (None, [VP, I, P]),
         "orc_dt": (D, [VP, D, P]),
+        "orc_step_local": (None, [VP, I, D]),
+        "orc_dt_local": (None, [VP, I, D, P]),
         "orc_set_threads": (None, [I]),
         "orc_max_threads": (I, []),
         "orc_free": (None, [VP]),
@@ -191,6 +193,17 @@ class Problem:
             d = _f64(dt)
             assert d.shape == (len(self.dims),)
             self._lib.orc_step_multi(self._h, int(nsteps), _p(d))
+
+    def step_local(self, nsteps, cfl):
+        """Local time stepping: each node advances with its own time step,
+        taken from the state at the start of every step."""
+        self._lib.orc_step_local(self._h, int(nsteps), float(cfl))
+
+    def dt_local(self, b, cfl):
+        """Per-node local time steps of block b, [nk][nj][ni]."""
+        out = np.empty(self.dims[b])
+        self._lib.orc_dt_local(self._h, b, float(cfl), _p(out))
+        return out
 
     def dt(self, cfl):
         """Returns (global dt, per-block dt) from the current state."""

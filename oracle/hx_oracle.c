@@ -69,6 +69,12 @@
  *       direction if t[a] > 0).  The paper's figures show aligned blocks
  *       only; the state, coordinates and gradients are physical quantities,
  *       so crossing a face only maps indices.
+ *   R15 local time step (Sec. 4.4 stores a time step per point and uses the
+ *       viscosity for it; no formula is printed): dt_i = CFL / (lambda_c +
+ *       lambda_v) with the convective radius of R8 at the node and, for
+ *       Navier-Stokes, lambda_v = (Ma/Re) max(4/3, gamma/Pr) (mu/rho)
+ *       sum_d (J |m_d|)^2; dt_i is taken from Q^n and held for the three
+ *       stages of a step.
  * Parity of the physical-face rules (R9, R10) is unpinned: the paper gives no
  * formulas for them.
  */
@@ -1051,41 +1057,102 @@ void orc_get_grad(void *h, int b, double *g) {
     memcpy(g, P->b[b].grad, sizeof(double) * 12 * npts(&P->b[b]));
 }
 
-/* Eq. (20) with dt[b] per block, nsteps steps. */
-void orc_step_multi(void *h, int nsteps, const double *dt) {
-    oproblem *P = (oproblem *)h;
+/* Convective spectral radius of node id of block B (reading R8):
+ * sum_d (|m_d.u| + c |m_d|) J. */
+static double lambda_c(const oproblem *P, const oblock *B, const int id[3], const double q[5]) {
+    prim_t s = to_prim(P, q);
+    const double J = jac_at(B, id);
+    double sum = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double m[3];
+        metric_at(B, id, d, m);
+        const double mm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+        sum += (fabs(m[0] * s.u + m[1] * s.v + m[2] * s.w) + s.c * mm) * J;
+    }
+    return sum;
+}
+
+/* Local time step of node id (reading R15). */
+static double local_dt(const oproblem *P, const oblock *B, const int id[3], const double q[5], double cfl) {
+    double lam = lambda_c(P, B, id, q);
+    if (P->viscous) {
+        prim_t s = to_prim(P, q);
+        const double J = jac_at(B, id);
+        double g2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            double m[3];
+            metric_at(B, id, d, m);
+            g2 += J * J * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+        }
+        const double gp = P->gamma / P->pr;
+        lam += P->mach / P->re * (gp > 4.0 / 3.0 ? gp : 4.0 / 3.0) * viscosity(P, s.T) / s.rho * g2;
+    }
+    return cfl / lam;
+}
+
+/* Eq. (20), nsteps steps.  Time step per block (dt[b]) or, when dtl is not
+ * NULL, per node: dtl[b] holds each node's local step of the state at the
+ * start of the step (reading R15), refreshed every step from cfl. */
+static void step_rk3(oproblem *P, int nsteps, const double *dt, double **dtl, double cfl) {
     double **Qc = state_ptrs(P, 0), **Qs = state_ptrs(P, 2);
     for (int it = 0; it < nsteps; ++it) {
         for (int b = 0; b < P->nb; ++b) memcpy(P->b[b].qn, P->b[b].q, sizeof(double) * 5 * npts(&P->b[b]));
+        if (dtl) {
+            for (int b = 0; b < P->nb; ++b) {
+                oblock *B = &P->b[b];
+                const size_t N = npts(B);
+                for (int k = 0; k < B->n[2]; ++k)
+                    for (int j = 0; j < B->n[1]; ++j)
+                        for (int i = 0; i < B->n[0]; ++i) {
+                            const int id[3] = {i, j, k};
+                            const size_t pp = pidx(B, id);
+                            double q[5];
+                            for (int c = 0; c < 5; ++c) q[c] = B->qn[c * N + pp];
+                            dtl[b][pp] = local_dt(P, B, id, q, cfl);
+                        }
+            }
+        }
         /* stage 1: Q1 = Qn + dt R(Qn) */
         rhs_all(P, Qc);
         for (int b = 0; b < P->nb; ++b) {
             oblock *B = &P->b[b];
-            const size_t M5 = 5 * npts(B);
-            for (size_t t = 0; t < M5; ++t) B->qs[t] = B->qn[t] + dt[b] * B->r[t];
+            const size_t N = npts(B), M5 = 5 * N;
+            for (size_t t = 0; t < M5; ++t) {
+                const double h = dtl ? dtl[b][t % N] : dt[b];
+                B->qs[t] = B->qn[t] + h * B->r[t];
+            }
         }
         bc_nodes(P, Qs);
         /* stage 2: Q2 = 3/4 Qn + 1/4 Q1 + 1/4 dt R(Q1) */
         rhs_all(P, Qs);
         for (int b = 0; b < P->nb; ++b) {
             oblock *B = &P->b[b];
-            const size_t M5 = 5 * npts(B);
-            for (size_t t = 0; t < M5; ++t)
-                B->qs[t] = 3.0 / 4.0 * B->qn[t] + 1.0 / 4.0 * B->qs[t] + 1.0 / 4.0 * dt[b] * B->r[t];
+            const size_t N = npts(B), M5 = 5 * N;
+            for (size_t t = 0; t < M5; ++t) {
+                const double h = dtl ? dtl[b][t % N] : dt[b];
+                B->qs[t] = 3.0 / 4.0 * B->qn[t] + 1.0 / 4.0 * B->qs[t] + 1.0 / 4.0 * h * B->r[t];
+            }
         }
         bc_nodes(P, Qs);
         /* stage 3: Q^{n+1} = 1/3 Qn + 2/3 Q2 + 2/3 dt R(Q2) */
         rhs_all(P, Qs);
         for (int b = 0; b < P->nb; ++b) {
             oblock *B = &P->b[b];
-            const size_t M5 = 5 * npts(B);
-            for (size_t t = 0; t < M5; ++t)
-                B->q[t] = 1.0 / 3.0 * B->qn[t] + 2.0 / 3.0 * B->qs[t] + 2.0 / 3.0 * dt[b] * B->r[t];
+            const size_t N = npts(B), M5 = 5 * N;
+            for (size_t t = 0; t < M5; ++t) {
+                const double h = dtl ? dtl[b][t % N] : dt[b];
+                B->q[t] = 1.0 / 3.0 * B->qn[t] + 2.0 / 3.0 * B->qs[t] + 2.0 / 3.0 * h * B->r[t];
+            }
         }
         bc_nodes(P, Qc);
     }
     free(Qc);
     free(Qs);
+}
+
+/* Eq. (20) with dt[b] per block, nsteps steps. */
+void orc_step_multi(void *h, int nsteps, const double *dt) {
+    step_rk3((oproblem *)h, nsteps, dt, NULL, 0.0);
 }
 
 void orc_step(void *h, int nsteps, double dt) {
@@ -1094,6 +1161,34 @@ void orc_step(void *h, int nsteps, double dt) {
     for (int b = 0; b < P->nb; ++b) d[b] = dt;
     orc_step_multi(h, nsteps, d);
     free(d);
+}
+
+/* Local time stepping (reading R15): nsteps steps, each node with its own
+ * time step from the state at the start of the step. */
+void orc_step_local(void *h, int nsteps, double cfl) {
+    oproblem *P = (oproblem *)h;
+    double **dtl = (double **)malloc(sizeof(double *) * (P->nb ? P->nb : 1));
+    for (int b = 0; b < P->nb; ++b) dtl[b] = (double *)malloc(sizeof(double) * npts(&P->b[b]));
+    step_rk3(P, nsteps, NULL, dtl, cfl);
+    for (int b = 0; b < P->nb; ++b) free(dtl[b]);
+    free(dtl);
+}
+
+/* Local time steps (reading R15) of the current state of block b,
+ * [nk][nj][ni]. */
+void orc_dt_local(void *h, int b, double cfl, double *out) {
+    oproblem *P = (oproblem *)h;
+    oblock *B = &P->b[b];
+    const size_t N = npts(B);
+    for (int k = 0; k < B->n[2]; ++k)
+        for (int j = 0; j < B->n[1]; ++j)
+            for (int i = 0; i < B->n[0]; ++i) {
+                const int id[3] = {i, j, k};
+                const size_t pp = pidx(B, id);
+                double q[5];
+                for (int c = 0; c < 5; ++c) q[c] = B->q[c * N + pp];
+                out[pp] = local_dt(P, B, id, q, cfl);
+            }
 }
 
 /* Reading R8: dt_out[b] = cfl / max over nodes of block b of
@@ -1109,18 +1204,10 @@ double orc_dt(void *h, double cfl, double *dt_out) {
             for (int j = 0; j < B->n[1]; ++j)
                 for (int i = 0; i < B->n[0]; ++i) {
                     const int id[3] = {i, j, k};
-                    const size_t p = pidx(B, id);
+                    const size_t pp = pidx(B, id);
                     double q[5];
-                    for (int c = 0; c < 5; ++c) q[c] = B->q[c * N + p];
-                    prim_t s = to_prim(P, q);
-                    const double J = jac_at(B, id);
-                    double sum = 0.0;
-                    for (int d = 0; d < 3; ++d) {
-                        double m[3];
-                        metric_at(B, id, d, m);
-                        const double mm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-                        sum += (fabs(m[0] * s.u + m[1] * s.v + m[2] * s.w) + s.c * mm) * J;
-                    }
+                    for (int c = 0; c < 5; ++c) q[c] = B->q[c * N + pp];
+                    const double sum = lambda_c(P, B, id, q);
                     if (sum > smax) smax = sum;
                 }
         const double dt = cfl / smax;

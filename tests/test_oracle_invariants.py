@@ -264,6 +264,64 @@ def test_topology_check_rejects_mismatch():
 
 # ---------------------------------------------------------------- time step (reading R8)
 
+def test_local_dt_minimum_is_the_global_dt():
+    """Reading R8 per node: the smallest local (Euler) time step of every
+    block is that block's global time step, exactly."""
+    w = W.batch(count=3, seed=11)
+    P = oracle.from_workload(w)
+    _, per = P.dt(0.7)
+    for b in range(len(w.blocks)):
+        assert P.dt_local(b, 0.7).min() == per[b]
+
+
+def test_local_dt_viscous_closed_form():
+    """Reading R15 on a uniform lattice at rest (rho = 1, T = 1, mu = 1, c = 1):
+    dt = CFL / (3c/h + (Ma/Re) max(4/3, gamma/Pr) (mu/rho) 3/h^2)."""
+    n, L = 10, 2.0
+    X, Y, Z = W.lattice((n, n, n), (L, L, L))
+    q = W.conservative(G, np.ones_like(X), 0.0, 0.0, 0.0, 1.0 / G)
+    mach, re, pr = 0.3, 50.0, 0.72
+    P = _single(np.stack([X, Y, Z]), q, (L, L, L), mach=mach, reynolds=re, prandtl=pr, viscous=True)
+    h = L / n
+    lam = 3.0 / h + mach / re * max(4.0 / 3.0, G / pr) * 3.0 / h ** 2
+    assert np.allclose(P.dt_local(0, 0.5), 0.5 / lam, rtol=1e-13)
+
+
+def test_local_step_equals_block_steps_when_uniform_per_block():
+    """Two independent periodic blocks, each with a spectral radius uniform
+    over its nodes (to rounding) but different between them, and a non-zero
+    residual (a shear flow with u + v = a, both positive): one local-time-
+    stepping step equals one step with each block's own time step."""
+    n, L = 12, 1.0
+    X, Y, Z = W.lattice((n, n, n), (L, L, L))
+    xyz = np.stack([X, Y, Z])
+    a = 0.5
+    u = a * (0.75 + 0.25 * np.sin(2 * np.pi * Y))   # in [a/2, a]: a - u is exact
+    v = a - u
+    qs = [W.conservative(G, np.ones_like(X), u, v, 0.0, 1.0 / G),
+          W.conservative(G, np.full_like(X, 0.5), u, v, 0.0, 1.0 / G)]
+    def problem():
+        P = oracle.Problem(gamma=G)
+        for b in range(2):
+            P.add_block(xyz)
+        for b in range(2):
+            for f, face in enumerate(W.periodic_faces((L, L, L), self_index=b)):
+                P.set_face(b, f, face.kind, face.nbr, face.nbr_face, face.translate)
+        P.check()
+        P.metrics()
+        for b in range(2):
+            P.set_state(b, qs[b])
+        return P
+    A, B = problem(), problem()
+    per = np.array([A.dt_local(b, 0.6).max() for b in range(2)])
+    assert all(np.ptp(A.dt_local(b, 0.6)) <= 1e-13 * per[b] for b in range(2)) and per[0] > 1.2 * per[1]
+    A.step_local(1, 0.6)
+    B.step(1, per)
+    for b in range(2):
+        qa, qb = A.get_state(b), B.get_state(b)
+        assert np.abs(qa - qb).max() <= 1e-14 * np.abs(qb).max()
+        assert np.abs(qa - qs[b]).max() > 1e-6   # the step moved the state
+
 def test_dt_closed_form_on_uniform_lattice():
     n, L = 12, 3.0
     X, Y, Z = W.lattice((n, n, n), (L, L, L))

@@ -42,6 +42,8 @@ MUTANTS = [
     ("viscous flux row", "fv[2] = m[0] * txy + m[1] * tyy + m[2] * tyz;", "fv[2] = m[0] * txy + m[1] * tyy + m[2] * txz;"),
     ("interface tangential flip", "nid[p] = t > 0 ? id[a] : N->n[p] - 1 - id[a];", "nid[p] = id[a];"),
     ("interface layer", "nid[p] = nside ? N->n[p] - 1 - l : l;", "nid[p] = nside ? N->n[p] - l : l;"),
+    ("local dt viscous factor", "(gp > 4.0 / 3.0 ? gp : 4.0 / 3.0)", "4.0 / 3.0"),
+    ("local dt block", "const double h = dtl ? dtl[b][t % N] : dt[b];", "const double h = dtl ? dtl[0][t % N] : dt[b];"),
     ("face flux pairing", "qr[c] = UR[c * L + f + 1 + O];", "qr[c] = UR[c * L + f + O];"),
 ]
 
