@@ -180,6 +180,24 @@ int hx_step_multi(hx_ctx* ctx, int nsteps, const double* dt_per_block);
  * NULL) gets the sum of the global dt over the steps. */
 int hx_step_cfl(hx_ctx* ctx, int nsteps, double cfl, int per_block, double* time_advanced);
 
+/* Local time stepping (Sec. 4.4 keeps a time step per grid point; for
+ * pseudo-time marching to a steady state): nsteps TVD-RK3 steps in which
+ * every node advances with its own time step, taken on the device from the
+ * state at the start of each step and held for its three stages:
+ * dt_i = cfl / (lambda_c + lambda_v), lambda_c = sum_d (|m_d.u| + c |m_d|) J
+ * as in hx_compute_dt, and for Navier-Stokes lambda_v = (Ma/Re)
+ * max(4/3, gamma/Pr) (mu/rho) sum_d (J |m_d|)^2.  The paper prints no
+ * formula; this is the library's reading.  Time is not consistent across
+ * nodes, so the result is a steady state's approach, not a transient.
+ * One CUDA graph per step; allocates one FP64 field on first use
+ * (HX_ERR_OOM).  Errors: HX_ERR_INVALID_ARG (nsteps < 0, cfl not positive),
+ * HX_ERR_NONFINITE / HX_ERR_UNPHYSICAL as hx_step. */
+int hx_step_local(hx_ctx* ctx, int nsteps, double cfl);
+
+/* The local time steps of hx_step_local for the current state of `block`,
+ * written to dt_out [nk][nj][ni] (host, or device when on_device != 0). */
+int hx_local_dt(hx_ctx* ctx, int block, double cfl, double* dt_out, int on_device);
+
 /* Root-mean-square residual of the current state over all nodes of all
  * blocks, per conservative variable: rms[c] = sqrt(sum R_c^2 / N)
  * (Fig. 2 calc_res; reduced on the device, Sec. 4.5.3).  rms has 5 entries. */

@@ -67,6 +67,7 @@ struct RKArgs {
     double* Qout;         // stage output, FP64
     float* Qfout;         // FP32 copy of the stage output (mixed form) or null
     const float* Aref;    // mixed form: the FP32 divergence of the rest state (rounding only), or null
+    const double* dtl;    // local time stepping: the time step of every node (field layout), or null
     double ca, cb, cc, gm1;
     unsigned* flags;
 };

@@ -291,7 +291,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
 #pragma unroll
                         for (int k = 0; k < 5; ++k) dv[k] -= (R)rk.Aref[k * fs + e];
                     }
-                    const double f = -rk.cc * B.dt * rk.metd[9 * fs + e];
+                    const double f = -rk.cc * (rk.dtl ? rk.dtl[e] : B.dt) * rk.metd[9 * fs + e];
                     double qo[5];
 #pragma unroll
                     for (int k = 0; k < 5; ++k) {

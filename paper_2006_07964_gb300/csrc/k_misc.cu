@@ -480,6 +480,43 @@ k_dt(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bloc
     }
 }
 
+// Local time step of every interior node (local time stepping): CFL over
+// the node's convective spectral radius (as in k_dt) plus, for
+// Navier-Stokes, the viscous one (Ma/Re) max(4/3, gamma/Pr) (mu/rho)
+// sum_d (J |m_d|)^2; from the FP64 state, CFL read from device memory.
+__global__ void __launch_bounds__(kThreads)
+k_dt_local(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks,
+           const double* __restrict__ Q, const double* __restrict__ met, long long fs, Gas gas,
+           const double* __restrict__ cfl, double* __restrict__ dtl) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const DevBlock& B = blocks[br.b];
+        const long long e = node_index(B, i, j, k);
+        const double irho = 1.0 / Q[e];
+        const double u = Q[fs + e] * irho, v = Q[2 * fs + e] * irho, w = Q[3 * fs + e] * irho;
+        const double p = (gas.gamma - 1.0) * (Q[4 * fs + e] - 0.5 * Q[e] * (u * u + v * v + w * w));
+        const double T = gas.gamma * p * irho;
+        const double c = sqrt(T);
+        const double J = met[9 * fs + e];
+        double lam = 0.0, g2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double mx = met[(3 * d) * fs + e], my = met[(3 * d + 1) * fs + e], mz = met[(3 * d + 2) * fs + e];
+            const double m2 = mx * mx + my * my + mz * mz;
+            lam += (fabs(mx * u + my * v + mz * w) + c * sqrt(m2)) * J;
+            g2 += J * J * m2;
+        }
+        if (gas.viscous) {
+            const double mu = gas.mu_law == 0 ? 1.0 : T * sqrt(T) * (1.0 + gas.suth) / (T + gas.suth);
+            lam += gas.mach / gas.re * fmax(gas.gamma / gas.pr, 4.0 / 3.0) * mu * irho * g2;
+        }
+        dtl[e] = cfl[0] / lam;
+    }
+}
+
 // dt of every block from the per-block maxima of k_dt: cfl / max (global
 // minimum when per_block == 0), written into the block table; the global dt
 // is added to the simulated-time accumulator.
@@ -672,6 +709,13 @@ cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, con
             k_grad<float, false><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)prim, (const float*)met,
                                                          fs, (float*)out, gs);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt_local(const Brick* bricks, int nb, const DevBlock* blocks, const double* Q, const double* met,
+                            long long fs, Gas gas, const double* cfl, double* dtl, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    k_dt_local<<<grid_for((long long)nb * kThreads), kThreads, 0, s>>>(bricks, nb, blocks, Q, met, fs, gas, cfl, dtl);
     return cudaGetLastError();
 }
 

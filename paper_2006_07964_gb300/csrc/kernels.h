@@ -75,6 +75,9 @@ cudaError_t launch_rhs_out(DevBlock B, const void* A, const float* Aref, bool fp
 cudaError_t launch_fill_fields(void* p, bool fp64, long long fs, int nf, const double* v, cudaStream_t s);
 cudaError_t launch_fill(void* p, bool fp64, long long n, double v, cudaStream_t s);
 // dt = cfl / max wave speed per block (or the global minimum) into the block table.
+// Local time step of every interior node into dtl (field layout), CFL read from *cfl.
+cudaError_t launch_dt_local(const Brick* bricks, int nb, const DevBlock* blocks, const double* Q, const double* met,
+                            long long fs, Gas gas, const double* cfl, double* dtl, cudaStream_t s);
 cudaError_t launch_setdt(DevBlock* blocks, int nb, const unsigned long long* bmax, const double* cfl, int per_block,
                          double* time_acc, unsigned* flags, cudaStream_t s);
 // sums[c] += sum over nodes of R_c^2 (R = -J (A - Aref)).

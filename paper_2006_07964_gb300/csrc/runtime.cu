@@ -89,6 +89,8 @@ struct hx_ctx {
 
     cudaGraphExec_t gexec = nullptr;
     cudaGraphExec_t gexec_cfl[2] = {nullptr, nullptr};   // step with on-device dt: global / per block
+    cudaGraphExec_t gexec_lts = nullptr;   // step with local time stepping
+    double* dtl = nullptr;                 // local time step of every node (allocated on first use)
     double* d_scal = nullptr;   // [0] cfl, [1] simulated-time accumulator, [2..6] residual sums
     std::vector<double> dt_dev;   // dt currently in the device block table
     int launches_per_step = 0;
@@ -311,7 +313,7 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
     return HX_OK;
 }
 
-int enqueue_step(hx_ctx* ctx, Prof* pf) {
+int enqueue_step(hx_ctx* ctx, Prof* pf, const double* dtl = nullptr) {
     static const double co[3][3] = {{1.0, 0.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
     static const int in_slot[3] = {0, 1, 2}, out_slot[3] = {1, 2, 0};
     double* q64[3] = {ctx->Qn, ctx->Qa, ctx->Qb};
@@ -324,6 +326,7 @@ int enqueue_step(hx_ctx* ctx, Prof* pf) {
         rk.Qout = q64[out_slot[st]];
         rk.Qfout = ctx->fp64() ? nullptr : ctx->Qf[out_slot[st]];
         rk.Aref = ctx->Aref;
+        rk.dtl = dtl;
         rk.ca = co[st][0];
         rk.cb = co[st][1];
         rk.cc = co[st][2];
@@ -457,10 +460,19 @@ int enqueue_cfl_step(hx_ctx* ctx, int per_block) {
     return enqueue_step(ctx, nullptr);
 }
 
+// One step of local time stepping: every node's time step from Q^n (CFL in
+// d_scal[0]), then the three stages with it.
+int enqueue_lts_step(hx_ctx* ctx) {
+    HX_CK(launch_dt_local(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->Qn, ctx->met, ctx->fs, ctx->gas, ctx->d_scal,
+                          ctx->dtl, ctx->stream));
+    return enqueue_step(ctx, nullptr, ctx->dtl);
+}
+
+// cfl_mode < 0: fixed dt; 0 / 1: on-device global / per-block dt; 2: local time stepping.
 int capture(hx_ctx* ctx, cudaGraphExec_t* out, int cfl_mode) {
     cudaGraph_t g = nullptr;
     HX_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = cfl_mode < 0 ? enqueue_step(ctx, nullptr) : enqueue_cfl_step(ctx, cfl_mode);
+    int rc = cfl_mode < 0 ? enqueue_step(ctx, nullptr) : cfl_mode == 2 ? enqueue_lts_step(ctx) : enqueue_cfl_step(ctx, cfl_mode);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
@@ -1025,6 +1037,38 @@ int hx_step_cfl(hx_ctx* ctx, int nsteps, double cfl, int per_block, double* time
     return rc;
 }
 
+static int ensure_dtl(hx_ctx* ctx) {
+    if (ctx->dtl) return HX_OK;
+    int rc = dalloc(ctx, (void**)&ctx->dtl, (size_t)ctx->fs * 8);
+    if (rc) return rc;
+    HX_CK(launch_fill(ctx->dtl, true, ctx->fs, 0.0, ctx->stream));
+    return HX_OK;
+}
+
+int hx_step_local(hx_ctx* ctx, int nsteps, double cfl) {
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (nsteps < 0 || !(cfl > 0) || !std::isfinite(cfl)) return fail(ctx, HX_ERR_INVALID_ARG, "bad nsteps or cfl");
+    if ((rc = autotune(ctx))) return rc;
+    if ((rc = ensure_dtl(ctx))) return rc;
+    if (!ctx->gexec_lts && (rc = capture(ctx, &ctx->gexec_lts, 2))) return rc;
+    HX_CK(cudaMemcpyAsync(ctx->d_scal, &cfl, sizeof cfl, cudaMemcpyHostToDevice, ctx->stream));
+    HX_CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned), ctx->stream));
+    for (int i = 0; i < nsteps; ++i) HX_CK(cudaGraphLaunch(ctx->gexec_lts, ctx->stream));
+    return read_flags(ctx);
+}
+
+int hx_local_dt(hx_ctx* ctx, int block, double cfl, double* dt_out, int on_device) {
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (!(cfl > 0) || !std::isfinite(cfl)) return fail(ctx, HX_ERR_INVALID_ARG, "bad cfl");
+    if ((rc = ensure_dtl(ctx))) return rc;
+    HX_CK(cudaMemcpyAsync(ctx->d_scal, &cfl, sizeof cfl, cudaMemcpyHostToDevice, ctx->stream));
+    HX_CK(launch_dt_local(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->Qn, ctx->met, ctx->fs, ctx->gas, ctx->d_scal,
+                          ctx->dtl, ctx->stream));
+    return get_field(ctx, block, ctx->dtl, true, 1, dt_out, on_device);
+}
+
 int hx_residual(hx_ctx* ctx, double* rms) {
     int rc = check_ready(ctx);
     if (rc) return rc;
@@ -1131,6 +1175,7 @@ void hx_destroy(hx_ctx* ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     for (auto& g : ctx->gexec_cfl)
         if (g) cudaGraphExecDestroy(g);
+    if (ctx->gexec_lts) cudaGraphExecDestroy(ctx->gexec_lts);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;

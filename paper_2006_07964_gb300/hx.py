@@ -31,7 +31,7 @@ EXPORTS = (
     "hx_set_state", "hx_get_state", "hx_get_metrics", "hx_compute_dt", "hx_step", "hx_step_multi", "hx_rhs",
     "hx_get_gradients", "hx_profile_step", "hx_launches_per_step", "hx_points", "hx_device_bytes",
     "hx_last_error", "hx_destroy", "hx_euler_rhs_periodic_noalloc", "hx_tuning", "hx_step_cfl", "hx_residual",
-    "hx_set_face_transform",
+    "hx_set_face_transform", "hx_step_local", "hx_local_dt",
 )
 
 
@@ -94,6 +94,8 @@ def load(path=None):
         "hx_euler_rhs_periodic_noalloc": (I, [I, I, I, D, VP, VP, VP, VP]),
         "hx_tuning": (I, [CTX, ctypes.POINTER(I), ctypes.POINTER(I), P]),
         "hx_step_cfl": (I, [CTX, I, D, I, P]),
+        "hx_step_local": (I, [CTX, I, D]),
+        "hx_local_dt": (I, [CTX, I, D, P, I]),
         "hx_residual": (I, [CTX, P]),
     }
     for name, (res, args) in sig.items():
@@ -241,6 +243,16 @@ class Context:
         t = ctypes.c_double()
         self._check(self._lib.hx_step_cfl(self._h, int(nsteps), float(cfl), int(bool(per_block)), ctypes.byref(t)))
         return t.value
+
+    def step_local(self, nsteps, cfl):
+        """nsteps RK3 steps of local time stepping (each node its own dt)."""
+        self._check(self._lib.hx_step_local(self._h, int(nsteps), float(cfl)))
+
+    def local_dt(self, block, cfl):
+        """Per-node local time steps of the current state, [nk][nj][ni]."""
+        out = np.empty(self.dims[block])
+        self._check(self._lib.hx_local_dt(self._h, block, float(cfl), _dp(out), 0))
+        return out
 
     def residual(self):
         """RMS of R over all nodes, per conservative variable (5 values)."""

@@ -364,6 +364,36 @@ def test_repeated_runs_are_bitwise_identical(name, precision):
         assert np.array_equal(ctx.get_state(b), q1[b]), (name, b)
 
 
+@pytest.mark.parametrize("name,steps", [("vortex32", 4), ("ragged_ns", 3), ("ogrid_s8", 3), ("rotated_ns", 2)])
+def test_local_time_stepping_parity(name, steps):
+    """Local time stepping: the per-node time steps of the initial state,
+    then the state after the steps (each node its own time step, refreshed
+    every step on the device), against the oracle's."""
+    w = CASES[name]()
+    ctx = hx.from_workload(w)
+    P = oracle.from_workload(w)
+    for b in range(len(w.blocks)):
+        ref = P.dt_local(b, 0.5)
+        assert np.abs(ctx.local_dt(b, 0.5) - ref).max() <= 1e-13 * ref.max(), (name, b)
+    ctx.step_local(steps, 0.5)
+    P.step_local(steps, 0.5)
+    for b in range(len(w.blocks)):
+        assert rel_linf(ctx.get_state(b), P.get_state(b)) < TOL, (name, b)
+
+
+def test_local_time_stepping_mixed_close():
+    """The mixed form under local time stepping stays within its FP32 bound
+    of the oracle (rel. L2 per variable after 5 steps of the vortex)."""
+    w = W.vortex(32)
+    ctx = hx.from_workload(w, precision="mixed")
+    P = oracle.from_workload(w)
+    ctx.step_local(5, 0.5)
+    P.step_local(5, 0.5)
+    a, b = ctx.get_state(0), P.get_state(0)
+    for v in (0, 1, 4):
+        assert np.linalg.norm(a[v] - b[v]) / np.linalg.norm(b[v]) < 1e-5, v
+
+
 # ---------------------------------------------------------------- error paths
 
 def test_error_topology():
