@@ -23,13 +23,6 @@ FluxShape flux_shape(int dir, int v) {
     return v == 0 ? FluxShape{8, 32} : v == 1 ? FluxShape{16, 16} : FluxShape{8, 16};
 }
 
-size_t flux_smem(bool fp64, int dir, int v, bool visc) {
-    const FluxShape sh = flux_shape(dir, v);
-    const int ring = sh.tp >= 8 ? 2 * sh.tp : 16;
-    const size_t plane = (size_t)ring * sh.na;
-    return (fp64 ? 8 : 4) * plane * ((visc ? 27 : 23) + (fp64 ? 7 : 0));
-}
-
 int flux_ctas_per_sm(bool fp64, int dir, int v, bool visc, bool rk, int scheme) {
     if (fp64)
         return dir == 0 ? flux_ctas_f64_d0(v, visc, rk, scheme) : dir == 1 ? flux_ctas_f64_d1(v, visc, rk, scheme)

@@ -32,7 +32,6 @@ struct FluxShape {
 
 constexpr int kFluxVariants = 3;
 FluxShape flux_shape(int dir, int variant);
-size_t flux_smem(bool fp64, int dir, int variant, bool visc);
 // CTAs per SM the variant can keep resident (0 if it cannot launch); also
 // sets the kernel's shared-memory opt-in.
 int flux_ctas_per_sm(bool fp64, int dir, int variant, bool visc, bool rk = false, int scheme = 0);
