@@ -355,6 +355,24 @@ k_normals(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__
     }
 }
 
+// Checking aid: NaN into every node of the bricks outside its block's
+// interior (the ghost shell), for nf fields.
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+k_poison(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, T* p, long long fs, int nf) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const DevBlock& B = blocks[br.b];
+        if (i >= 0 && i < B.n[0] && j >= 0 && j < B.n[1] && k >= 0 && k < B.n[2]) continue;
+        const long long e = node_index(B, i, j, k);
+        for (int f = 0; f < nf; ++f) p[f * fs + e] = T(NAN);
+    }
+}
+
 // ---------------------------------------------------------------- primitives
 template <class R>
 __global__ void __launch_bounds__(kThreads)
@@ -672,6 +690,17 @@ cudaError_t launch_normals(const Brick* bricks, int nb, const DevBlock* blocks, 
                            double* nrm, cudaStream_t s) {
     if (nb <= 0) return cudaSuccess;
     k_normals<<<grid_for((long long)nb * kThreads), kThreads, 0, s>>>(bricks, nb, blocks, met, fs, nrm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poison(const Brick* bricks, int nb, const DevBlock* blocks, void* p, bool fp64, long long fs,
+                          int nf, cudaStream_t s) {
+    if (nb <= 0 || !p) return cudaSuccess;
+    const int g = grid_for((long long)nb * kThreads);
+    if (fp64)
+        k_poison<double><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (double*)p, fs, nf);
+    else
+        k_poison<float><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (float*)p, fs, nf);
     return cudaGetLastError();
 }
 

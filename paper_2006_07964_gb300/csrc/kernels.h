@@ -59,6 +59,9 @@ cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, con
 // stress tensor and work + heat-flux vector (9 fields, stress_mode = true).
 cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, const void* prim, const void* met,
                         bool fp64, long long fs, void* out, bool stress_mode, Gas gas, cudaStream_t s);
+// Checking aid: NaN into the ghost shell of nf fields (bricks cover the padded box).
+cudaError_t launch_poison(const Brick* bricks, int nb, const DevBlock* blocks, void* p, bool fp64, long long fs,
+                          int nf, cudaStream_t s);
 // Far-field boundary nodes after a stage.
 cudaError_t launch_bc_farfield(const NodeItem* items, int n, const DevBlock* blocks, double* Q, float* Qf,
                                const double* met, long long fs, Gas gas, cudaStream_t s);

@@ -11,6 +11,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hx.h"
 #include "kernels.h"
 
@@ -73,6 +75,8 @@ struct hx_ctx {
     int ntiles[3][kFluxVariants] = {};
     Brick *d_int = nullptr, *d_prim = nullptr;
     int n_int = 0, n_prim = 0;
+    Brick* d_shell = nullptr;   // debug_poison: bricks over every block's padded box
+    int n_shell = 0;
     NodeItem* d_bc = nullptr;       // far-field boundary nodes
     int n_bc = 0;
     Brick *d_ghost = nullptr, *d_prep = nullptr;   // ghost slabs; interior + ghost slabs
@@ -247,6 +251,7 @@ struct Prof {
     cudaEvent_t start_ev = nullptr;
     void begin(int kind) {
         if (!on) return;
+        nvtxRangePushA(kKindName[kind]);
         Rec r{kind, nullptr, nullptr};
         cudaEventCreate(&r.a);
         cudaEventCreate(&r.b);
@@ -256,7 +261,14 @@ struct Prof {
     void end() {
         if (!on) return;
         cudaEventRecord(recs.back().b, s);
+        nvtxRangePop();
     }
+};
+
+// NVTX range over an entry point (visible to nsys / ncu range filters).
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
 };
 
 // The residual of one stage from stage slot `in`: the ghosts of the
@@ -270,6 +282,14 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
     const bool visc = ctx->cfg.viscous != 0;
     void* Qs = stencil_state(ctx, in);
     const void* M = stencil_met(ctx);
+    if (prep && ctx->cfg.debug_poison) {   // checking aid: every ghost NaN before the halo fill
+        HX_CK(launch_poison(ctx->d_shell, ctx->n_shell, ctx->d_blocks, Qs, f64, ctx->fs, 5, s));
+        HX_CK(launch_poison(ctx->d_shell, ctx->n_shell, ctx->d_blocks, ctx->A, f64, ctx->fs, 5, s));
+        if (visc) {
+            HX_CK(launch_poison(ctx->d_shell, ctx->n_shell, ctx->d_blocks, ctx->prim, f64, ctx->fs, 4, s));
+            HX_CK(launch_poison(ctx->d_shell, ctx->n_shell, ctx->d_blocks, ctx->grad, f64, ctx->fs, 12, s));
+        }
+    }
     if (prep) {
         if (pf) pf->begin(K_PREP);
         if (visc)
@@ -846,6 +866,16 @@ int hx_finalize(hx_ctx* ctx) {
     if ((rc = upload(ctx, &ctx->d_prim, bp))) return rc;
     ctx->d_prep = ctx->d_prim;
     if ((rc = upload(ctx, &ctx->d_ghost, bg))) return rc;
+    if (ctx->cfg.debug_poison) {
+        std::vector<Brick> sh;
+        for (int b = 0; b < nb; ++b) {
+            const HostBlock& H = ctx->blocks[b];
+            const int lo[3] = {-G, -G, -G}, hi[3] = {H.n[0] + G, H.n[1] + G, H.n[2] + G};
+            add_bricks(sh, b, lo, hi);
+        }
+        ctx->n_shell = (int)sh.size();
+        if ((rc = upload(ctx, &ctx->d_shell, sh))) return rc;
+    }
     std::vector<NodeItem> bc;
     for (int b = 0; b < nb; ++b) {
         const HostBlock& H = ctx->blocks[b];
@@ -865,13 +895,15 @@ int hx_finalize(hx_ctx* ctx) {
     ctx->n_bc = (int)bc.size();
     if ((rc = upload(ctx, &ctx->d_bc, bc))) return rc;
     HX_CK(cudaStreamSynchronize(ctx->stream));
-    ctx->launches_per_step = 3 * (1 + (visc ? 1 : 0) + 3 + (ctx->n_bc ? 1 : 0));
+    ctx->launches_per_step = 3 * (1 + (visc ? 1 : 0) + 3 + (ctx->n_bc ? 1 : 0) +
+                                  (ctx->cfg.debug_poison ? (visc ? 4 : 2) : 0));
     ctx->finalized = true;
     return HX_OK;
 }
 
 int hx_compute_metrics(hx_ctx* ctx) {
     if (!ctx) return HX_ERR_INVALID_ARG;
+    NvtxScope range("hx_compute_metrics");
     if (!ctx->finalized) return fail(ctx, HX_ERR_STATE, "call hx_finalize first");
     int rc = set_device(ctx);
     if (rc) return rc;
@@ -1010,15 +1042,18 @@ int hx_compute_dt(hx_ctx* ctx, double cfl, double* dt_global, double* dt_per_blo
 
 int hx_step(hx_ctx* ctx, int nsteps, double dt) {
     if (!ctx) return HX_ERR_INVALID_ARG;
+    NvtxScope range("hx_step");
     return step_common(ctx, nsteps, std::vector<double>(ctx->blocks.size(), dt));
 }
 
 int hx_step_multi(hx_ctx* ctx, int nsteps, const double* dt_per_block) {
     if (!ctx || !dt_per_block) return HX_ERR_INVALID_ARG;
+    NvtxScope range("hx_step_multi");
     return step_common(ctx, nsteps, std::vector<double>(dt_per_block, dt_per_block + ctx->blocks.size()));
 }
 
 int hx_step_cfl(hx_ctx* ctx, int nsteps, double cfl, int per_block, double* time_advanced) {
+    NvtxScope range("hx_step_cfl");
     int rc = check_ready(ctx);
     if (rc) return rc;
     if (nsteps < 0 || !(cfl > 0) || !std::isfinite(cfl)) return fail(ctx, HX_ERR_INVALID_ARG, "bad nsteps or cfl");
@@ -1046,6 +1081,7 @@ static int ensure_dtl(hx_ctx* ctx) {
 }
 
 int hx_step_local(hx_ctx* ctx, int nsteps, double cfl) {
+    NvtxScope range("hx_step_local");
     int rc = check_ready(ctx);
     if (rc) return rc;
     if (nsteps < 0 || !(cfl > 0) || !std::isfinite(cfl)) return fail(ctx, HX_ERR_INVALID_ARG, "bad nsteps or cfl");
@@ -1087,6 +1123,7 @@ int hx_residual(hx_ctx* ctx, double* rms) {
 }
 
 int hx_rhs(hx_ctx* ctx, int block, double* r_out, int on_device) {
+    NvtxScope range("hx_rhs");
     int rc = check_ready(ctx);
     if (rc) return rc;
     if (block < 0 || block >= (int)ctx->blocks.size() || !r_out) return fail(ctx, HX_ERR_INVALID_ARG, "bad block or pointer");

@@ -40,7 +40,7 @@ class hx_config(ctypes.Structure):
         ("gamma", ctypes.c_double), ("mach", ctypes.c_double), ("reynolds", ctypes.c_double),
         ("prandtl", ctypes.c_double), ("viscous", ctypes.c_int), ("mu_law", ctypes.c_int),
         ("sutherland_s", ctypes.c_double), ("precision", ctypes.c_int), ("scheme", ctypes.c_int),
-        ("mem_cap_bytes", ctypes.c_size_t), ("autotune", ctypes.c_int),
+        ("mem_cap_bytes", ctypes.c_size_t), ("autotune", ctypes.c_int), ("debug_poison", ctypes.c_int),
     ]
 
 
@@ -315,12 +315,12 @@ def euler_rhs_periodic_noalloc(q, met, r_out, gamma=1.4, stream=None):
     return r_out
 
 
-def from_workload(w, precision="fp64", stream=None, autotune=1, mem_cap_bytes=0, scheme=0):
+def from_workload(w, precision="fp64", stream=None, autotune=1, mem_cap_bytes=0, scheme=0, debug_poison=0):
     """Context with the blocks, faces, metrics and initial state of a
     workload from ``paper_2006_07964_gb300.workloads``."""
     ctx = Context(stream=stream, gamma=w.gamma, mach=w.mach, reynolds=w.reynolds, prandtl=w.prandtl,
                   viscous=int(w.viscous), mu_law=w.mu_law, sutherland_s=w.sutherland_s, precision=precision,
-                  autotune=autotune, mem_cap_bytes=mem_cap_bytes, scheme=scheme)
+                  autotune=autotune, mem_cap_bytes=mem_cap_bytes, scheme=scheme, debug_poison=debug_poison)
     for blk in w.blocks:
         ctx.add_block(blk.xyz)
     for b, blk in enumerate(w.blocks):

@@ -394,6 +394,27 @@ def test_local_time_stepping_mixed_close():
         assert np.linalg.norm(a[v] - b[v]) / np.linalg.norm(b[v]) < 1e-5, v
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["vortex32", "ragged_ns", "split_ns", "rotated_euler", "rotated_ns", "ogrid_s8",
+                                  "shock_warped"])
+def test_poisoned_ghosts_change_nothing(name, precision):
+    """Halo completeness: with every ghost node of the stencil state,
+    primitives, node stress and accumulator set to NaN before each stage, the
+    residual and two steps are bitwise those of the normal run (a ghost the
+    halo fill misses, and a stencil reads, would turn them non-finite)."""
+    w = CASES[name]()
+    ref = hx.from_workload(w, precision=precision)
+    chk = hx.from_workload(w, precision=precision, debug_poison=1)
+    nb = len(w.blocks)
+    for b in range(nb):
+        assert np.array_equal(chk.rhs(b), ref.rhs(b)), (name, b)
+    dt, _ = ref.compute_dt(0.5)
+    ref.step(2, dt)
+    chk.step(2, dt)
+    for b in range(nb):
+        assert np.array_equal(chk.get_state(b), ref.get_state(b)), (name, b)
+
+
 # ---------------------------------------------------------------- error paths
 
 def test_error_topology():
