@@ -292,37 +292,49 @@ __device__ __forceinline__ void weno_pair(double w0, double w1, double w2, doubl
     right = fma(r.nR, r.dL * inv, r.uR2);
 }
 
-// The five characteristic fields of a node with one FP64 division: each
-// field's dL dR is brought to [1, 2) by its binary exponent (integer pipe;
-// dL dR >= 1e-41 from eps), the five reciprocals come from one division of
-// their product and the prefix products, and each is scaled back by its
-// exponent.  W[s][l]: stencil node s = 0..4 (i-2..i+2), field l.
+// num / D[l] for N positive FP64 values with one division: each D[l] is
+// brought to [1, 2) by its binary exponent (integer pipe; the WENO
+// denominators lie far inside the exponent range), the reciprocals come from
+// one division of their product and the prefix products, and each is scaled
+// back by its exponent.
+template <int N>
+__device__ __forceinline__ void batch_recip(const double (&D)[N], double num, double (&inv)[N]) {
+    double m[N], P[N];
+    int ex[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+        const long long b = __double_as_longlong(D[l]);
+        ex[l] = (int)(b >> 52) & 0x7ff;
+        m[l] = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+        P[l] = l == 0 ? m[0] : P[l - 1] * m[l];
+    }
+    double I = num / P[N - 1];
+#pragma unroll
+    for (int l = N - 1; l > 0; --l) {
+        inv[l] = I * P[l - 1];
+        I *= m[l];
+    }
+    inv[0] = I;
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+        inv[l] = __longlong_as_double(__double_as_longlong(inv[l]) - ((long long)(ex[l] - 1023) << 52));
+}
+
+// The five characteristic fields of a node with one FP64 division.
+// W[s][l]: stencil node s = 0..4 (i-2..i+2), field l.
 __device__ __forceinline__ void weno_pair5(const double (&W)[5][5], double (&WL)[5], double (&WR)[5]) {
     WenoParts r[5];
-    double D[5];
-    int ex[5];
+    double D[5], inv[5];
 #pragma unroll
     for (int l = 0; l < 5; ++l) {
         r[l] = weno_parts(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l]);
-        const long long b = __double_as_longlong(r[l].dL * r[l].dR);
-        ex[l] = (int)(b >> 52) & 0x7ff;
-        D[l] = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+        D[l] = r[l].dL * r[l].dR;
     }
-    const double P1 = D[0] * D[1], P2 = P1 * D[2], P3 = P2 * D[3], P4 = P3 * D[4];
-    double I = 0.125 / P4, inv[5];
-    inv[4] = I * P3;
-    I *= D[4];
-    inv[3] = I * P2;
-    I *= D[3];
-    inv[2] = I * P1;
-    I *= D[2];
-    inv[1] = I * D[0];
-    inv[0] = I * D[1];
+    batch_recip<5>(D, 0.125, inv);
 #pragma unroll
     for (int l = 0; l < 5; ++l) {
-        const double v = __longlong_as_double(__double_as_longlong(inv[l]) - ((long long)(ex[l] - 1023) << 52));
-        WL[l] = fma(r[l].nL, r[l].dR * v, r[l].uL2);
-        WR[l] = fma(r[l].nR, r[l].dL * v, r[l].uR2);
+        WL[l] = fma(r[l].nL, r[l].dR * inv[l], r[l].uL2);
+        WR[l] = fma(r[l].nR, r[l].dL * inv[l], r[l].uR2);
     }
 }
 
@@ -362,32 +374,69 @@ __device__ __forceinline__ void weno_pair5(const float (&W)[5][5], float (&WL)[5
 
 // One WENO5 value with its own indicators (original AFWENO, Fig. 9): the
 // left-biased value at i+1/2 (LEFT) or the right-biased value at i-1/2 of
-// the stencil W[-2..2] of node i.
+// the stencil W[-2..2] of node i, in the form of the pair above:
+// value = u2 + n / (8 d).
+template <class R>
+struct WenoSide {
+    R n, d, u2;
+};
+
 template <class R, bool LEFT>
-__device__ __forceinline__ R weno_one(R w0, R w1, R w2, R w3, R w4) {
-    const R eps = R(1.0e-6);
-    const R a1 = w0 - R(2) * w1 + w2, c1 = w0 - R(4) * w1 + R(3) * w2;
-    const R a2 = w1 - R(2) * w2 + w3, c2 = w1 - w3;
-    const R a3 = w2 - R(2) * w3 + w4, c3 = R(3) * w2 - R(4) * w3 + w4;
-    R s1 = eps + R(13.0 / 12.0) * a1 * a1 + R(0.25) * c1 * c1;
-    R s2 = eps + R(13.0 / 12.0) * a2 * a2 + R(0.25) * c2 * c2;
-    R s3 = eps + R(13.0 / 12.0) * a3 * a3 + R(0.25) * c3 * c3;
+__device__ __forceinline__ WenoSide<R> weno_side(R w0, R w1, R w2, R w3, R w4) {
+    const R eps4 = R(4.0e-6);
+    const R d10 = w1 - w0, d21 = w2 - w1, d32 = w3 - w2, d43 = w4 - w3;
+    const R a1 = d21 - d10, a2 = d32 - d21, a3 = d43 - d32;
+    const R c1 = R(2) * d21 + a1, c2 = d21 + d32, c3 = R(-2) * d32 + a3;
+    const R k = R(13.0 / 3.0);
+    R s1 = a1 * (k * a1) + (c1 * c1 + eps4);
+    R s2 = a2 * (k * a2) + (c2 * c2 + eps4);
+    R s3 = a3 * (k * a3) + (c3 * c3 + eps4);
     s1 *= s1;
     s2 *= s2;
     s3 *= s3;
     const R p12 = s1 * s2, p13 = s1 * s3, p23 = s2 * s3;
+    const R e1 = a1 - a2, e2 = a2 - a3;
+    WenoSide<R> r;
     if (LEFT) {
-        const R u1 = R(0.375) * w0 - R(1.25) * w1 + R(1.875) * w2;
-        const R u2 = R(-0.125) * w1 + R(0.75) * w2 + R(0.375) * w3;
-        const R u3 = R(0.375) * w2 + R(0.75) * w3 - R(0.125) * w4;
-        const R t1 = R(0.0625) * p23, t2 = R(0.625) * p13, t3 = R(0.3125) * p12;
-        return (t1 * u1 + t2 * u2 + t3 * u3) / (t1 + t2 + t3);
+        r.d = R(10) * p13 + (R(5) * p12 + p23);
+        r.n = R(3) * (p23 * e1) + R(5) * (p12 * e2);
+        r.u2 = R(0.125) * (R(3) * d32 + d21) + w2;
     } else {
-        const R u1 = R(0.375) * w4 - R(1.25) * w3 + R(1.875) * w2;
-        const R u2 = R(-0.125) * w3 + R(0.75) * w2 + R(0.375) * w1;
-        const R u3 = R(0.375) * w2 + R(0.75) * w1 - R(0.125) * w0;
-        const R t1 = R(0.0625) * p12, t2 = R(0.625) * p13, t3 = R(0.3125) * p23;
-        return (t1 * u1 + t2 * u2 + t3 * u3) / (t1 + t2 + t3);
+        r.d = R(10) * p13 + (R(5) * p23 + p12);
+        r.n = -(R(3) * (p12 * e2) + R(5) * (p23 * e1));
+        r.u2 = R(-0.125) * (R(3) * d21 + d32) + w2;
+    }
+    return r;
+}
+
+// The ten values of a face (five fields, each side with its own stencil:
+// left from nodes i-2..i+2, right from i-1..i+3): one FP64 division, or two
+// hardware reciprocals per field in FP32.  W[s][l]: nodes s = 0..5.
+__device__ __forceinline__ void weno_face10(const double (&W)[6][5], double (&WL)[5], double (&WR)[5]) {
+    WenoSide<double> L[5], Rt[5];
+    double D[10], inv[10];
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        L[l] = weno_side<double, true>(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l]);
+        Rt[l] = weno_side<double, false>(W[1][l], W[2][l], W[3][l], W[4][l], W[5][l]);
+        D[l] = L[l].d;
+        D[5 + l] = Rt[l].d;
+    }
+    batch_recip<10>(D, 0.125, inv);
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        WL[l] = fma(L[l].n, inv[l], L[l].u2);
+        WR[l] = fma(Rt[l].n, inv[5 + l], Rt[l].u2);
+    }
+}
+
+__device__ __forceinline__ void weno_face10(const float (&W)[6][5], float (&WL)[5], float (&WR)[5]) {
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        const WenoSide<float> L = weno_side<float, true>(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l]);
+        const WenoSide<float> Rt = weno_side<float, false>(W[1][l], W[2][l], W[3][l], W[4][l], W[5][l]);
+        WL[l] = fmaf(L.n, __fdividef(0.125f, L.d), L.u2);
+        WR[l] = fmaf(Rt.n, __fdividef(0.125f, Rt.d), Rt.u2);
     }
 }
 

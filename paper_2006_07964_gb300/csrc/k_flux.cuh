@@ -245,11 +245,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                                        W[s + 2]);
                         }
                         R WL[5], WR[5];
-#pragma unroll
-                        for (int l = 0; l < 5; ++l) {
-                            WL[l] = weno_one<R, true>(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l]);
-                            WR[l] = weno_one<R, false>(W[1][l], W[2][l], W[3][l], W[4][l], W[5][l]);
-                        }
+                        weno_face10(W, WL, WR);
                         cb.back(WL, ql);
                         cb.back(WR, qr);
                     }
