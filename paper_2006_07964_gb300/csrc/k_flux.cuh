@@ -167,13 +167,21 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         sF[3 * PL + s0] = q[3] * th + mz * cb.p;
                         sF[4 * PL + s0] = (q[4] + cb.p) * th;
                     }
-                    if (vnode) {
+                    // viscous node flux m.(tau, beta); FP32 writes it after the WENO
+                    // of the node, so that the stress loads have arrived by then
+                    auto put_fv = [&]() {
+                        if (!vnode) return;
                         sFv[s0] = mx * S[0] + my * S[3] + mz * S[4];
                         sFv[PL + s0] = mx * S[3] + my * S[1] + mz * S[5];
                         sFv[2 * PL + s0] = mx * S[4] + my * S[5] + mz * S[2];
                         sFv[3 * PL + s0] = mx * S[6] + my * S[7] + mz * S[8];
+                    };
+                    constexpr bool LATE_FV = sizeof(R) == 4;
+                    if (!LATE_FV) put_fv();
+                    if (SCH == 1 || p < -1 || p > n) {   // WENO only where a face needs it
+                        if (LATE_FV) put_fv();
+                        continue;
                     }
-                    if (SCH == 1 || p < -1 || p > n) continue;   // WENO only where a face needs it
                     if (pre) cb.set_normal(sKn[s0], sKn[PL + s0], sKn[2 * PL + s0]);
                     R W[5][5];
 #pragma unroll
@@ -190,6 +198,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     cb.back(WR, U);
 #pragma unroll
                     for (int f = 0; f < 5; ++f) sUR[f * PL + s0] = U[f];
+                    if (LATE_FV) put_fv();
                 }
             }
             __syncthreads();
