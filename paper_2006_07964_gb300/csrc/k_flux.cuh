@@ -275,6 +275,15 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                 const int sp = LY::idx(p, a), sm1 = LY::idx(p - 1, a);
                 const int s1 = LY::idx(p + 1, a), s2 = LY::idx(p + 2, a), s3 = LY::idx(p + 3, a);
                 const int t1 = LY::idx(p - 1, a), t2 = LY::idx(p - 2, a), t3 = LY::idx(p - 3, a);
+                // The accumulator is loaded first, so that it arrives while the
+                // differences below are formed from shared memory.  The fused
+                // RK sweep loads it, and its RK inputs, where they are used:
+                // hoisting them there measured slower (registers).
+                R acc[5];
+                if (accumulate && !RK) {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) acc[k] = A[k * fs + e];
+                }
                 R dv[5];
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
@@ -286,7 +295,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         auto fv = [&](int s) { return Fv[LY::idx(p + s, a)]; };
                         div -= dline<R>(fv, p, n, lo, hi);
                     }
-                    dv[k] = accumulate ? A[k * fs + e] + div : div;
+                    dv[k] = accumulate ? (RK ? A[k * fs + e] : acc[k]) + div : div;
                 }
                 if (!RK) {
 #pragma unroll
