@@ -277,10 +277,11 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                 const int t1 = LY::idx(p - 1, a), t2 = LY::idx(p - 2, a), t3 = LY::idx(p - 3, a);
                 // The accumulator is loaded first, so that it arrives while the
                 // differences below are formed from shared memory.  The fused
-                // RK sweep loads it, and its RK inputs, where they are used:
-                // hoisting them there measured slower (registers).
+                // RK sweep's other inputs are loaded where they are used:
+                // hoisting them too costs registers (80 instead of 72 in FP32,
+                // one CTA less per SM) and measured slower.
                 R acc[5];
-                if (accumulate && !RK) {
+                if (accumulate) {
 #pragma unroll
                     for (int k = 0; k < 5; ++k) acc[k] = A[k * fs + e];
                 }
@@ -295,7 +296,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         auto fv = [&](int s) { return Fv[LY::idx(p + s, a)]; };
                         div -= dline<R>(fv, p, n, lo, hi);
                     }
-                    dv[k] = accumulate ? (RK ? A[k * fs + e] : acc[k]) + div : div;
+                    dv[k] = accumulate ? acc[k] + div : div;
                 }
                 if (!RK) {
 #pragma unroll
