@@ -53,8 +53,8 @@ RK_FLOPS = 30   # R = -J A and the three-term combination, five components
 # and profiles/flux_mixed_tgv128.md give the command).  Another workload, or a
 # kernel changed since the capture, reports null.
 TRAFFIC_TGV128 = {
-    ("fp64", "flux_xi"): 528.3e6, ("fp64", "flux_eta"): 639.7e6, ("fp64", "flux_zeta_rk"): 761.3e6,
-    ("mixed", "flux_xi"): 196.8e6, ("mixed", "flux_eta"): 241.6e6, ("mixed", "flux_zeta_rk"): 579.7e6,
+    ("fp64", "flux_xi"): 531.0e6, ("fp64", "flux_eta"): 642.6e6, ("fp64", "flux_zeta_rk"): 761.2e6,
+    ("mixed", "flux_xi"): 193.3e6, ("mixed", "flux_eta"): 241.7e6, ("mixed", "flux_zeta_rk"): 581.7e6,
 }
 
 
