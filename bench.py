@@ -85,6 +85,8 @@ WORKLOADS = {
     "vortex32": ("isentropic vortex, Euler, warped periodic 32^3 block", lambda W: W.vortex(32)),
     "ogrid": ("cylinder O-grid, NS Ma0.2 Re3900, 8 blocks, 3,538,944 nodes", lambda W: W.ogrid()),
     "batch64": ("64 isentropic-vortex instances, edges from {24..96}, seeded", lambda W: W.batch(64)),
+    "shock512": ("two Sod shock tubes in a warped periodic 512x64x64 box, Euler",
+                 lambda W: W.shocktube((512, 64, 64), amp=0.02)),
 }
 
 
