@@ -53,7 +53,9 @@ enum {
     HX_ERR_CUDA = -6,         /* a CUDA runtime call failed                      */
     HX_ERR_NONFINITE = -7,    /* a step produced a non-finite state              */
     HX_ERR_UNPHYSICAL = -8,   /* non-positive density or pressure after a step   */
-    HX_ERR_TIMEOUT = -9       /* reserved: a bounded device wait gave up         */
+    HX_ERR_TIMEOUT = -9,      /* reserved: a bounded device wait gave up         */
+    HX_ERR_BOUNDS = -10       /* checking builds (HX_BOUNDS) only: a kernel computed
+                                 a node offset outside its field                  */
 };
 
 /* Face kinds (Sec. 4.2: connecting faces and physical faces). */

@@ -33,6 +33,8 @@ struct DevBlock {
     // negative (the CGNS 1-to-1 convention); identity for aligned blocks
     signed char tf[6][3];
     double dt;        // time step of this block
+    long long lim;    // elements per field of the layout (checking builds: node offsets must be below)
+    unsigned* flags;  // device error word (checking builds record FLAG_BOUNDS there), or null
 };
 
 struct Gas {
@@ -56,7 +58,7 @@ struct NodeItem {      // a node on a physical face: block, indices, face direct
     int b, i, j, k, dir, side, pad0, pad1;
 };
 
-enum : int { FLAG_NONFINITE = 1, FLAG_BAD_GRID = 2, FLAG_UNPHYSICAL = 4 };
+enum : int { FLAG_NONFINITE = 1, FLAG_BAD_GRID = 2, FLAG_UNPHYSICAL = 4, FLAG_BOUNDS = 8 };
 
 // The RK3 stage combination (Eq. (20)) fused into the last sweep:
 // Q_out = ca Q^n + cb Q^(k) + cc dt R, R = -J A, in FP64.
@@ -81,8 +83,24 @@ __device__ __forceinline__ bool nonfinite_bits(double x) {
 // bits 8.. translation index (coordinates).
 enum : int { HM_COPY = 0, HM_WALL = 1, HM_FARFIELD = 2, HM_TRANSLATE = 3, HM_REFLECT = 4 };
 
+// A node offset into a field of block B's layout.  Checking builds
+// (HX_BOUNDS) verify it lies inside the field; an offset outside records
+// FLAG_BOUNDS and is replaced by 0 (a padding element), so the access stays
+// inside the buffer and the host reports HX_ERR_BOUNDS.  No trap.
+__host__ __device__ inline long long hx_chk(const DevBlock& B, long long e) {
+#if defined(HX_BOUNDS) && defined(__CUDA_ARCH__)
+    if (e < 0 || e >= B.lim) {
+        if (B.flags) atomicOr(B.flags, (unsigned)FLAG_BOUNDS);
+        return 0;
+    }
+#else
+    (void)B;
+#endif
+    return e;
+}
+
 __host__ __device__ inline long long node_index(const DevBlock& B, int i, int j, int k) {
-    return B.base + i + (long long)j * B.sj + (long long)k * B.sk;
+    return hx_chk(B, B.base + i + (long long)j * B.sj + (long long)k * B.sk);
 }
 
 // Index in the neighbour N (extents nN) across face f of block B of the

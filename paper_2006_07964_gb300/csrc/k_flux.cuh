@@ -115,7 +115,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     LY::split(it, cnt, p, a);
                     p += first;
                     if (a0 + a >= na || p > n + 2) continue;
-                    const long long e = e0 + p * sd + a * sa;
+                    const long long e = hx_chk(B, e0 + p * sd + a * sa);
                     const int s = LY::idx(p, a);
 #pragma unroll
                     for (int f = 0; f < 5; ++f) sQ[f * PL + s] = Q[f * fs + e];
@@ -145,7 +145,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     const bool vnode = VISC && !((lo && p < 0) || (hi && p >= n));
                     R S[9];
                     if (vnode) {   // issued first; consumed after the node flux
-                        const long long e = e0 + p * sd + a * sa;
+                        const long long e = hx_chk(B, e0 + p * sd + a * sa);
 #pragma unroll
                         for (int f = 0; f < 9; ++f) S[f] = stress[f * fs + e];
                     }
@@ -271,7 +271,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                 LY::split(it, TP, p, a);
                 p += base - 2;
                 if (a0 + a >= na || p < 0 || p >= n) continue;
-                const long long e = e0 + p * sd + a * sa;
+                const long long e = hx_chk(B, e0 + p * sd + a * sa);
                 const int sp = LY::idx(p, a), sm1 = LY::idx(p - 1, a);
                 const int s1 = LY::idx(p + 1, a), s2 = LY::idx(p + 2, a), s3 = LY::idx(p + 3, a);
                 const int t1 = LY::idx(p - 1, a), t2 = LY::idx(p - 2, a), t3 = LY::idx(p - 3, a);

@@ -251,8 +251,10 @@ struct CoordView {
     // sixth-order derivative of coordinate c along axis a at (i, j, k)
     __device__ __forceinline__ double dx(int c, int a, int i, int j, int k) const {
         const long long st = a == 0 ? 1 : (a == 1 ? B.sj : B.sk);
-        const double* p = X + c * fs + node_index(B, i, j, k);
-        return d6<double>(p[-3 * st], p[-2 * st], p[-st], p[st], p[2 * st], p[3 * st]);
+        const long long e = node_index(B, i, j, k);
+        const double* p = X + c * fs;
+        auto f = [&](int s) { return p[hx_chk(B, e + s * st)]; };
+        return d6<double>(f(-3), f(-2), f(-1), f(1), f(2), f(3));
     }
     // outer derivative along ao of (d x_ci / d a_in) * x_cm
     __device__ __forceinline__ double prod_d(int ci, int ain, int cm, int ao, int i, int j, int k) const {
@@ -330,7 +332,7 @@ k_normals(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__
                 if (a != d && (id[a] < 0 || id[a] >= B.n[a])) line = false;
             if (!line) continue;
             const long long st = d == 0 ? 1 : (d == 1 ? B.sj : B.sk);
-            const double* m = met + 3 * d * fs + e;
+            const double* m = met + 3 * d * fs + e;   // e is checked; the stencil offsets below are too
             const double mx = m[0], my = m[fs], mz = m[2 * fs];
             const double imm = hrsqrt(mx * mx + my * my + mz * mz);
             double* o = nrm + 7 * d * fs + e;
@@ -341,8 +343,9 @@ k_normals(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__
                 double mf[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const double* q = m + c * fs;
-                    mf[c] = mid6<double>(q[-2 * st], q[-st], q[0], q[st], q[2 * st], q[3 * st]);
+                    const double* q = met + (3 * d + c) * fs;
+                    auto f = [&](int s) { return q[hx_chk(B, e + s * st)]; };
+                    mf[c] = mid6<double>(f(-2), f(-1), f(0), f(1), f(2), f(3));
                 }
                 const double mm2 = mf[0] * mf[0] + mf[1] * mf[1] + mf[2] * mf[2];
                 const double im = hrsqrt(mm2);
@@ -418,8 +421,8 @@ k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
             const bool lo = (B.phys >> (2 * a)) & 1, hi = (B.phys >> (2 * a + 1)) & 1;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const R* f0 = prim + v * fs + e;
-                auto f = [&](int s) { return f0[s * st]; };
+                const R* f0 = prim + v * fs;
+                auto f = [&](int s) { return f0[hx_chk(B, e + s * st)]; };
                 dc[v][a] = dline<R>(f, id[a], B.n[a], lo, hi);
             }
         }

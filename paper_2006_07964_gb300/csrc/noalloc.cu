@@ -110,6 +110,8 @@ extern "C" int hx_euler_rhs_periodic_noalloc(int ni, int nj, int nk, double gamm
     B.sk = (int)sk;
     B.base = XOFF + G * sj + G * sk;
     const long long fs = rup(sk * (nk + 2 * G), 64);
+    B.lim = fs;
+    B.flags = nullptr;
     const int n0 = nk * ((nj + kNA - 1) / kNA);
     const int n1 = nk * ((ni + kNA - 1) / kNA);
     const int n2 = nj * ((ni + kNA - 1) / kNA);

@@ -532,6 +532,7 @@ int read_flags(hx_ctx* ctx) {
     unsigned flags = 0;
     HX_CK(cudaMemcpyAsync(&flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream));
     HX_CK(cudaStreamSynchronize(ctx->stream));
+    if (flags & FLAG_BOUNDS) return fail(ctx, HX_ERR_BOUNDS, "a node offset outside its field (checking build)");
     if (flags & FLAG_NONFINITE) return fail(ctx, HX_ERR_NONFINITE, "non-finite state after a step");
     if (flags & FLAG_UNPHYSICAL) return fail(ctx, HX_ERR_UNPHYSICAL, "non-positive density or pressure after a step");
     return HX_OK;
@@ -828,7 +829,13 @@ int hx_finalize(hx_ctx* ctx) {
     }
     // ---- work lists
     std::vector<DevBlock> tab;
-    for (auto& H : ctx->blocks) tab.push_back(H.dev);
+    for (auto& H : ctx->blocks) {
+        H.dev.lim = ctx->fs;
+        H.dev.flags = ctx->d_flags;
+        H.cdev.lim = ctx->fsc;
+        H.cdev.flags = ctx->d_flags;
+        tab.push_back(H.dev);
+    }
     if ((rc = upload(ctx, &ctx->d_blocks, tab))) return rc;
     ctx->dt_dev.assign(nb, 0.0);
     for (int d = 0; d < 3; ++d)
@@ -931,6 +938,10 @@ int hx_compute_metrics(hx_ctx* ctx) {
     for (int m = 1; m <= 3; ++m) {
         std::vector<HaloItem> items;
         coord_halo_items(ctx, m, items);
+        for (const HaloItem& it : items)
+            if (it.dst < 0 || it.dst >= ctx->fsc || it.src < 0 || it.src >= ctx->fsc || it.aux < 0 ||
+                it.aux >= ctx->fsc)
+                return fail(ctx, HX_ERR_TOPOLOGY, "a ghost coordinate outside the coordinate layout");
         HaloItem* di = nullptr;
         if ((rc = upload(ctx, &di, items))) return rc;
         tmp.emplace_back((void*)di, items.size() * sizeof(HaloItem));
@@ -959,6 +970,7 @@ int hx_compute_metrics(hx_ctx* ctx) {
     dfree(ctx, dc, ctab.size() * sizeof(DevBlock));
     dfree(ctx, dbm, bm.size() * sizeof(Brick));
     for (auto& t : tmp) dfree(ctx, t.first, t.second);
+    if (flags & FLAG_BOUNDS) return fail(ctx, HX_ERR_BOUNDS, "a node offset outside its field (checking build)");
     if (flags & FLAG_BAD_GRID) return fail(ctx, HX_ERR_BAD_GRID, "non-positive Jacobian (J^-1 <= 0) at some node");
     for (auto& H : ctx->blocks) std::vector<double>().swap(H.xyz);
     ctx->metrics_done = true;

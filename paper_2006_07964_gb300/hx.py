@@ -21,6 +21,7 @@ HX_OK = 0
 ERRORS = {
     -1: "HX_ERR_INVALID_ARG", -2: "HX_ERR_STATE", -3: "HX_ERR_TOPOLOGY", -4: "HX_ERR_BAD_GRID",
     -5: "HX_ERR_OOM", -6: "HX_ERR_CUDA", -7: "HX_ERR_NONFINITE", -8: "HX_ERR_UNPHYSICAL", -9: "HX_ERR_TIMEOUT",
+    -10: "HX_ERR_BOUNDS",
 }
 FACE = {"periodic": 0, "interface": 1, "wall": 2, "farfield": 3}
 HX_FP64, HX_MIXED = 0, 1
@@ -63,7 +64,7 @@ def load(path=None):
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or os.environ.get("HX_LIB") or LIB_PATH   # HX_LIB: another build (the checking one)
     if not os.path.exists(path):
         raise OSError("libhx.so is not built (%s); run paper_2006_07964_gb300.build.build()" % path)
     lib = ctypes.CDLL(path)

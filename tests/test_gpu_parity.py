@@ -9,6 +9,10 @@ difference of O(1) fluxes that cancels to O(Ma) at low Mach).  Sizes span
 several tiles with ragged tails; full sizes of the benchmark workloads are
 compared on whole fields (the oracle is fast enough), plus multi-block,
 physical faces, per-block time steps and the error paths of the ABI."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -415,6 +419,26 @@ def test_poisoned_ghosts_change_nothing(name, precision):
     chk.step(2, dt)
     for b in range(nb):
         assert np.array_equal(chk.get_state(b), ref.get_state(b)), (name, b)
+
+
+@pytest.mark.slow
+def test_checked_build_runs_clean():
+    """Memory safety without a sanitizer: the library rebuilt with every
+    computed node offset range-checked (HX_BOUNDS: an offset outside its
+    field records HX_ERR_BOUNDS and is redirected inside the buffer, no trap)
+    passes the residual, step, gradient, metric, local-time-step and
+    poisoned-ghost parity tests of every case."""
+    lib = build.build(checked=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, HX_LIB=lib)
+    check = "from paper_2006_07964_gb300 import hx; import os; assert hx.load()._name == os.environ['HX_LIB']"
+    r = subprocess.run([sys.executable, "-c", check], cwd=root, env=env, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    sel = "(rhs_parity or steps_parity or gradient_parity or metrics_parity or local_time or poisoned) and not checked"
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "gpu",
+                        "tests/test_gpu_parity.py", "-k", sel], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=1500)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
 
 
 # ---------------------------------------------------------------- error paths
