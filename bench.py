@@ -50,11 +50,12 @@ RK_FLOPS = 30   # R = -J A and the three-term combination, five components
 # DRAM bytes (read + write) of one launch of each sweep on the Taylor-Green
 # 128^3 workload, from one ncu capture of the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/flux_fp64_tgv128.md
-# and profiles/flux_mixed_tgv128.md give the command).  Another workload, or a
-# kernel changed since the capture, reports null.
+# and profiles/flux_mixed_tgv128.md give the command).  The captured launches
+# are those of the second RK stage, whose fused zeta sweep reads Q^(k).
+# Another workload, or a kernel changed since the capture, reports null.
 TRAFFIC_TGV128 = {
     ("fp64", "flux_xi"): 531.0e6, ("fp64", "flux_eta"): 642.6e6, ("fp64", "flux_zeta_rk"): 761.2e6,
-    ("mixed", "flux_xi"): 193.3e6, ("mixed", "flux_eta"): 241.7e6, ("mixed", "flux_zeta_rk"): 581.7e6,
+    ("mixed", "flux_xi"): 194.6e6, ("mixed", "flux_eta"): 241.9e6, ("mixed", "flux_zeta_rk"): 573.9e6,
 }
 
 
@@ -71,11 +72,13 @@ def rk_extra_bytes_per_node(precision):
     """Bytes the fused zeta sweep adds for R = -J A and the RK3 stage: it
     reads A without writing it (-5 words), and reads Q^n, J and writes
     Q^(k+1) in FP64.  In the FP64 form the stage input Q^(k) is the stencil
-    state itself; the mixed form reads it in FP64 besides its FP32 copy, and
-    writes the FP32 copy of the output and reads the rest-state residual."""
+    state itself.  The mixed form reads J in FP32 and Q^(k) in FP64 besides
+    its FP32 copy (in two of the three stages: the first one's Q^(k) is
+    Q^n), writes the FP32 copy of the output and reads the rest-state
+    residual.  Mean over the three stages, as the launch time is."""
     if precision == "fp64":
         return -5 * 8 + (5 + 1 + 5) * 8
-    return -5 * 4 + (5 + 5 + 1 + 5) * 8 + 5 * 4 + 5 * 4
+    return -5 * 4 + (5 + 5 * 2 / 3 + 5) * 8 + 4 + 5 * 4 + 5 * 4
 
 
 WORKLOADS = {

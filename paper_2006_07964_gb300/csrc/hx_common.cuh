@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fpconv.h"
+
 namespace hx {
 
 // ---------------------------------------------------------------------------
@@ -71,8 +73,15 @@ struct RKArgs {
     const float* Aref;    // mixed form: the FP32 divergence of the rest state (rounding only), or null
     const double* dtl;    // local time stepping: the time step of every node (field layout), or null
     double ca, cb, cc, gm1;
+    float ccf;            // -cc in FP32 (the mixed form's FP32 increment)
     unsigned* flags;
 };
+
+// L2 prefetch hint for one global address: no register result, nothing to
+// wait for.  The address must lie inside a device allocation.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
 
 // Non-finite test on the exponent bits (integer pipe, not the FP64 unit).
 __device__ __forceinline__ bool nonfinite_bits(double x) {

@@ -64,16 +64,19 @@ struct FluxLayout {
 // state and the face metric, two independent WENOs per face, Fig. 9).
 // Resident CTAs per SM that the register allocation must allow.  FP64: two
 // of 256 threads (128 registers) or three of 128, so that the FP64 pipe
-// always has a second CTA's warps.  FP32: no target (0); the compiler's own
-// allocation (72-80 registers, three CTAs of 256) measured as fast as a
-// 64-register target and faster than an explicit 85-register one.
-template <class R, int NT>
+// always has a second CTA's warps.  FP32 Navier-Stokes with 128 threads:
+// seven (72 registers), which is what its shared memory allows; left free,
+// the allocation drifts between 72 and 80 registers (six CTAs) with small
+// code changes.  Other FP32 sweeps: no target (0); the compiler's own
+// allocation measured as fast as a 64-register target and faster than an
+// explicit 85-register one, and Euler sweeps keep 56-64 registers.
+template <class R, int NT, bool VISC>
 constexpr int flux_min_ctas() {
-    return sizeof(R) == 8 ? (NT >= 256 ? 2 : 3) : 0;
+    return sizeof(R) == 8 ? (NT >= 256 ? 2 : 3) : (VISC && NT < 256 ? 7 : 0);
 }
 
 template <class R, int DIR, int TP, int NA, bool VISC, bool RK, int SCH>
-__global__ void __launch_bounds__(TP * NA, flux_min_ctas<R, TP * NA>())
+__global__ void __launch_bounds__(TP * NA, flux_min_ctas<R, TP * NA, VISC>())
 k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int ntiles,
        const R* __restrict__ Q, const R* __restrict__ met, const R* __restrict__ nrm, long long fs,
        const R* __restrict__ stress, R* __restrict__ A, int accumulate, GasR<R> gs, RKArgs rk) {
@@ -130,6 +133,60 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                             for (int f = 0; f < 4; ++f) sKf[f * PL + s] = nr[(3 + f) * fs];
                         }
                     }
+                }
+            }
+            // ---- L2 prefetches (FP32 sweeps; each thread owns one node of
+            // every step): what this chunk's output step reads from global
+            // memory (the accumulator, the fused RK stage's inputs), and what
+            // the next chunk's load and node steps read (state, metric,
+            // stress).  Issued now, they arrive while the stencil phases run
+            // (measured on the 128^3 Taylor-Green sweeps: eta 0.124 -> 0.116
+            // ms, zeta + RK 0.214 -> 0.198 ms).
+            if (sizeof(R) == 4) {
+                // Opaque copies of the thread index and the field stride, so
+                // that none of this address arithmetic is shared with the
+                // other steps or hoisted out of the chunk loop, where it
+                // would hold registers through the stencil phases.
+                int tq = tid;
+                long long fq = fs;
+                asm volatile("" : "+r"(tq), "+l"(fq));
+                int p, a;
+                LY::split(tq, TP, p, a);
+                const bool line = a0 + a < na;
+                const int po = base - 2 + p;   // this chunk's output node
+                if ((accumulate || RK) && line && po >= 0 && po < n) {
+                    const long long e = hx_chk(B, e0 + po * sd + a * sa);
+                    if (accumulate) {
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) prefetch_l2(A + k * fq + e);
+                    }
+                    if (RK) {
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            prefetch_l2(rk.Qn + k * fq + e);
+                            if (rk.cb != 0.0) prefetch_l2(rk.Qk + k * fq + e);
+                            if (rk.Aref) prefetch_l2(rk.Aref + k * fq + e);
+                        }
+                        prefetch_l2(met + 9 * fq + e);
+                        if (rk.dtl) prefetch_l2(rk.dtl + e);
+                    }
+                }
+                // The next chunk's inputs: not in the fused RK sweep, which
+                // already prefetches its stage inputs (with them as well it
+                // measured 10 % slower).
+                const int pl = base + TP + 3 + p;   // the next chunk's load node
+                if (!RK && line && pl <= n + 2) {
+                    const long long e = hx_chk(B, e0 + pl * sd + a * sa);
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) prefetch_l2(Q + f * fq + e);
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) prefetch_l2(met + (3 * DIR + f) * fq + e);
+                }
+                const int pn = base + TP + 1 + p;   // the next chunk's node step
+                if (!RK && VISC && line && pn <= n + 2 && !(hi && pn >= n)) {
+                    const long long e = hx_chk(B, e0 + pn * sd + a * sa);
+#pragma unroll
+                    for (int f = 0; f < 9; ++f) prefetch_l2(stress + f * fq + e);
                 }
             }
             __syncthreads();
@@ -306,13 +363,28 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
 #pragma unroll
                         for (int k = 0; k < 5; ++k) dv[k] -= (R)rk.Aref[k * fs + e];
                     }
-                    const double f = -rk.cc * (rk.dtl ? rk.dtl[e] : B.dt) * rk.metd[9 * fs + e];
                     double qo[5];
+                    if constexpr (sizeof(R) == 4) {
+                        // Mixed form: the increment -cc dt J A is formed in FP32,
+                        // the precision A has; its combination with Q^n and Q^(k)
+                        // is FP64, one or two FMAs per field.  The format
+                        // conversions run on the integer pipe (fpconv.h): the
+                        // hardware ones would take FP64 slots.
+                        const float f =
+                            rk.ccf * hx_f64_to_f32(rk.dtl ? rk.dtl[e] : B.dt) * met[9 * fs + e];
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        double v = rk.ca * rk.Qn[k * fs + e] + f * (double)dv[k];
-                        if (rk.cb != 0.0) v += rk.cb * rk.Qk[k * fs + e];
-                        qo[k] = v;
+                        for (int k = 0; k < 5; ++k) {
+                            const double r = hx_f32_to_f64(f * dv[k]);
+                            qo[k] = fma(rk.ca, rk.Qn[k * fs + e], rk.cb != 0.0 ? fma(rk.cb, rk.Qk[k * fs + e], r) : r);
+                        }
+                    } else {
+                        const double f = -rk.cc * (rk.dtl ? rk.dtl[e] : B.dt) * rk.metd[9 * fs + e];
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            double v = rk.ca * rk.Qn[k * fs + e] + f * (double)dv[k];
+                            if (rk.cb != 0.0) v += rk.cb * rk.Qk[k * fs + e];
+                            qo[k] = v;
+                        }
                     }
                     if (B.wall) {   // node indices of this output (line groups start at sweep index 0)
                         const int ni_ = DIR == 0 ? p : T.i0 + a;
@@ -337,7 +409,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         float qv[5];
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
-                            qv[k] = (float)qo[k];
+                            qv[k] = hx_f64_to_f32(qo[k]);
                             rk.Qfout[k * fs + e] = qv[k];
                         }
                         if (!bad && !(qv[0] > 0.0f &&

@@ -152,7 +152,7 @@ __global__ void k_bc_farfield(const NodeItem* __restrict__ items, int n, const D
         farfield_state(gs, gas.mach, qi, m[0] * im, m[1] * im, m[2] * im, qb);
         for (int c = 0; c < 5; ++c) {
             Q[c * fs + e] = qb[c];
-            if (Qf) Qf[c * fs + e] = (float)qb[c];
+            if (Qf) Qf[c * fs + e] = hx_f64_to_f32(qb[c]);
         }
     }
 }

@@ -350,6 +350,7 @@ int enqueue_step(hx_ctx* ctx, Prof* pf, const double* dtl = nullptr) {
         rk.ca = co[st][0];
         rk.cb = co[st][1];
         rk.cc = co[st][2];
+        rk.ccf = (float)-co[st][2];
         rk.gm1 = ctx->gas.gamma - 1.0;
         rk.flags = ctx->d_flags;
         int rc = enqueue_rhs(ctx, in_slot[st], &rk, pf);

@@ -345,6 +345,26 @@ def test_mixed_precision_ns_rhs_close(name):
         assert err < 1e-5 * scale, (name, b, err, scale)
 
 
+@pytest.mark.parametrize("name", ["tgv24", "ogrid_s8", "rotated_ns"])
+def test_mixed_stage_copy_equals_cuda_cast(name):
+    """The mixed form's RK stage writes the FP32 stencil copy of its FP64
+    output with an integer-pipe conversion (fpconv.h).  After two steps, the
+    residual evaluated from that copy equals, bit for bit, the residual from
+    the copy hx_set_state makes of the same FP64 state with CUDA's own
+    conversion; the O-grid adds its wall and far-field nodes."""
+    w = CASES[name]()
+    ctx = hx.from_workload(w, precision="mixed")
+    nb = len(w.blocks)
+    dt, _ = ctx.compute_dt(0.5)
+    ctx.step(2, dt)
+    r_step = [ctx.rhs(b) for b in range(nb)]
+    q = [ctx.get_state(b) for b in range(nb)]
+    for b in range(nb):
+        ctx.set_state(b, q[b])
+    for b in range(nb):
+        assert np.array_equal(ctx.rhs(b), r_step[b]), (name, b)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["vortex32", "ragged_ns", "rotated_ns", "ogrid_s8"])
 def test_repeated_runs_are_bitwise_identical(name, precision):
