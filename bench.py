@@ -235,9 +235,10 @@ def roofline_for(ctx, w, precision, steps, dt, peaks):
     return out
 
 
-def cpu_baseline(w, seconds_target=15.0):
+def cpu_baseline(w, seconds_target=15.0, single_thread=True):
     """The FP64 oracle as it stands on this host's cores: whole RK3 steps of
-    the same workload until about `seconds_target` of CPU time."""
+    the same workload until about `seconds_target` of CPU time; then, on one
+    thread, one more whole step (the single-core figure)."""
     import oracle
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
@@ -251,8 +252,17 @@ def cpu_baseline(w, seconds_target=15.0):
         el = time.perf_counter() - t0
         if el > seconds_target or steps >= 50:
             break
-    return {"value": w.npts * 3 * steps / el / 1e6, "unit": "Mpts/s", "cores": oracle.max_threads(),
-            "kind": "oracle", "sample": "%d full RK3 step(s) of the %d-node workload, %.1f s" % (steps, w.npts, el)}
+    out = {"value": w.npts * 3 * steps / el / 1e6, "unit": "Mpts/s", "cores": oracle.max_threads(),
+           "kind": "oracle", "sample": "%d full RK3 step(s) of the %d-node workload, %.1f s" % (steps, w.npts, el)}
+    if single_thread:
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        P.step(1, dt)
+        el1 = time.perf_counter() - t0
+        oracle.set_threads(threads)
+        out["single_thread"] = {"value": w.npts * 3 / el1 / 1e6, "unit": "Mpts/s", "cores": 1,
+                                "sample": "1 full RK3 step of the same workload, %.1f s" % el1}
+    return out
 
 
 def _rel_errors(a, b):
