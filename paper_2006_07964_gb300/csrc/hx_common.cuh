@@ -74,6 +74,9 @@ struct RKArgs {
     const double* dtl;    // local time stepping: the time step of every node (field layout), or null
     double ca, cb, cc, gm1;
     float ccf;            // -cc in FP32 (the mixed form's FP32 increment)
+    float* primout;       // mixed Navier-Stokes, a stage whose output feeds the next: the FP32
+                          // (u, v, w, T) of the output at the node, so that the next stage's
+                          // prep fills only the ghosts; or null
     unsigned* flags;
 };
 

@@ -412,6 +412,14 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                             qv[k] = hx_f64_to_f32(qo[k]);
                             rk.Qfout[k * fs + e] = qv[k];
                         }
+                        if constexpr (sizeof(R) == 4) {
+                            if (rk.primout) {   // the next stage's primitives, from the FP32 copy as in k_prep
+                                float pv[4];
+                                primitives(gs, qv, pv);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) rk.primout[k * fs + e] = pv[k];
+                            }
+                        }
                         if (!bad && !(qv[0] > 0.0f &&
                                       qv[4] * qv[0] - 0.5f * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) > 0.0f))
                             atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);

@@ -135,9 +135,12 @@ __device__ void farfield_state(const GasR<R>& gs, R mach, const R qi[5], R nx, R
 // the 1D characteristic rule from the updated node next to it (FP64), and
 // its FP32 copy in the mixed form.  Wall nodes are handled in the sweep.
 __global__ void k_bc_farfield(const NodeItem* __restrict__ items, int n, const DevBlock* __restrict__ blocks,
-                              double* Q, float* Qf, const double* __restrict__ met, long long fs, Gas gas) {
+                              double* Q, float* Qf, float* primf, const double* __restrict__ met, long long fs,
+                              Gas gas) {
     GasR<double> gs;
     gs.init(gas);
+    GasR<float> gsf;
+    gsf.init(gas);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const NodeItem it = items[t];
         const DevBlock& B = blocks[it.b];
@@ -150,9 +153,16 @@ __global__ void k_bc_farfield(const NodeItem* __restrict__ items, int n, const D
         const double im = (side ? 1.0 : -1.0) / sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
         for (int c = 0; c < 5; ++c) qi[c] = Q[c * fs + ei];
         farfield_state(gs, gas.mach, qi, m[0] * im, m[1] * im, m[2] * im, qb);
+        float qf[5];
         for (int c = 0; c < 5; ++c) {
             Q[c * fs + e] = qb[c];
-            if (Qf) Qf[c * fs + e] = hx_f64_to_f32(qb[c]);
+            qf[c] = hx_f64_to_f32(qb[c]);
+            if (Qf) Qf[c * fs + e] = qf[c];
+        }
+        if (Qf && primf) {   // the node's FP32 primitives, when the next stage's prep skips the interior
+            float pv[4];
+            primitives(gsf, qf, pv);
+            for (int c = 0; c < 4; ++c) primf[c * fs + e] = pv[c];
         }
     }
 }
@@ -670,9 +680,9 @@ cudaError_t launch_halo_coords(const HaloItem* items, int n, double* X, long lon
 }
 
 cudaError_t launch_bc_farfield(const NodeItem* items, int n, const DevBlock* blocks, double* Q, float* Qf,
-                               const double* met, long long fs, Gas gas, cudaStream_t s) {
+                               float* primf, const double* met, long long fs, Gas gas, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_bc_farfield<<<grid_for(n), kThreads, 0, s>>>(items, n, blocks, Q, Qf, met, fs, gas);
+    k_bc_farfield<<<grid_for(n), kThreads, 0, s>>>(items, n, blocks, Q, Qf, primf, met, fs, gas);
     return cudaGetLastError();
 }
 

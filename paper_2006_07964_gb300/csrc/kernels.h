@@ -64,7 +64,7 @@ cudaError_t launch_poison(const Brick* bricks, int nb, const DevBlock* blocks, v
                           int nf, cudaStream_t s);
 // Far-field boundary nodes after a stage.
 cudaError_t launch_bc_farfield(const NodeItem* items, int n, const DevBlock* blocks, double* Q, float* Qf,
-                               const double* met, long long fs, Gas gas, cudaStream_t s);
+                               float* primf, const double* met, long long fs, Gas gas, cudaStream_t s);
 // Ghosts of the stencil state and (prim != null) primitives over the bricks
 // of the interior and the ghost slabs.
 cudaError_t launch_prep(const Brick* bricks, int nb, const DevBlock* blocks, void* Q, bool fp64, long long fs,

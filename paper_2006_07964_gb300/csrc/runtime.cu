@@ -276,7 +276,10 @@ struct NvtxScope {
 // its halo), then the three flux sweeps.  rk == null: A holds the
 // accumulated divergence.  With rk, the zeta sweep finishes R = -J A and
 // the RK3 stage into rk->Qout.
-int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = true) {
+// prim_interior = false: the primitives of the interior nodes are already
+// in place (the previous stage's epilogue wrote them), and the prep fills
+// the ghosts only.
+int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = true, bool prim_interior = true) {
     cudaStream_t s = ctx->stream;
     const bool f64 = ctx->fp64();
     const bool visc = ctx->cfg.viscous != 0;
@@ -292,8 +295,10 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
     }
     if (prep) {
         if (pf) pf->begin(K_PREP);
-        if (visc)
+        if (visc && prim_interior)
             HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, ctx->gas, s));
+        else if (visc)
+            HX_CK(launch_prep(ctx->d_ghost, ctx->n_ghost, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, ctx->gas, s));
         else
             HX_CK(launch_prep(ctx->d_ghost, ctx->n_ghost, ctx->d_blocks, Qs, f64, ctx->fs, M, nullptr, ctx->gas, s));
         if (pf) pf->end();
@@ -338,6 +343,9 @@ int enqueue_step(hx_ctx* ctx, Prof* pf, const double* dtl = nullptr) {
     static const int in_slot[3] = {0, 1, 2}, out_slot[3] = {1, 2, 0};
     double* q64[3] = {ctx->Qn, ctx->Qa, ctx->Qb};
     cudaStream_t s = ctx->stream;
+    // Mixed Navier-Stokes: stages 1 and 2 write the primitives of their
+    // output in their epilogue, and stages 2 and 3 skip the interior prep.
+    const bool fuse_prim = !ctx->fp64() && ctx->cfg.viscous != 0;
     for (int st = 0; st < 3; ++st) {
         RKArgs rk{};
         rk.Qn = ctx->Qn;
@@ -353,12 +361,13 @@ int enqueue_step(hx_ctx* ctx, Prof* pf, const double* dtl = nullptr) {
         rk.ccf = (float)-co[st][2];
         rk.gm1 = ctx->gas.gamma - 1.0;
         rk.flags = ctx->d_flags;
-        int rc = enqueue_rhs(ctx, in_slot[st], &rk, pf);
+        rk.primout = fuse_prim && st < 2 ? (float*)ctx->prim : nullptr;
+        int rc = enqueue_rhs(ctx, in_slot[st], &rk, pf, true, !(fuse_prim && st > 0));
         if (rc) return rc;
         if (ctx->n_bc) {
             if (pf) pf->begin(K_BC);
-            HX_CK(launch_bc_farfield(ctx->d_bc, ctx->n_bc, ctx->d_blocks, rk.Qout, rk.Qfout, ctx->met, ctx->fs,
-                                     ctx->gas, s));
+            HX_CK(launch_bc_farfield(ctx->d_bc, ctx->n_bc, ctx->d_blocks, rk.Qout, rk.Qfout, rk.primout, ctx->met,
+                                     ctx->fs, ctx->gas, s));
             if (pf) pf->end();
         }
     }
