@@ -76,8 +76,12 @@ typedef struct {
     int viscous;          /* 0: Euler, 1: Navier-Stokes                                 */
     int mu_law;           /* 0: mu = 1, 1: Sutherland mu = T^1.5 (1+S)/(T+S)            */
     double sutherland_s;  /* S of Sutherland's law (110.4/288.15)                       */
-    int precision;        /* HX_FP64, or HX_MIXED: FP32 state, fluxes and WENO with FP32
-                             accumulation; FP64 metrics, Jacobian and RK combination    */
+    int precision;        /* HX_FP64, or HX_MIXED: FP32 stencil state, fluxes, WENO and
+                             accumulation; FP64 metrics and FP64 state.  The RK stage
+                             forms its increment -c dt J A in FP32 (the precision of A)
+                             and combines it with Q^n and Q^(k) in FP64 (Eq. (20)); its
+                             FP32 copy of the new state rounds to nearest, with
+                             magnitudes below 2^-126 stored as zero                  */
     int scheme;           /* 0: modified AFWENO (characteristic space at the node, shared
                              indicators, Figs. 10-11); 1: the original AFWENO
                              (characteristic space at the face, two WENOs per face,
