@@ -37,9 +37,14 @@ struct FluxLayout {
     // fields per ring slot: Q 5, metric 3, node flux 5, U^L (then h) 5, U^R 5, viscous node flux 4;
     // FP64 adds the stored unit normals of the node (3) and of its + face (4)
     static constexpr int NF_INV = 23, NF_VISC = 27, NF_NRM = 7;
+    static_assert((NA & (NA - 1)) == 0 && (RING & (RING - 1)) == 0, "power-of-two line count and ring");
+    // Slot of node p: (p mod RING); DIR 0 rotates odd lines by RING/2 (the
+    // XOR of the top slot bit, written as an add inside the mask).  The line
+    // base has no bits in common with the slot, so each index is an add and
+    // one three-input logic operation.
     __device__ static __forceinline__ int idx(int p, int a) {
-        const int s = (p + 4 * RING) & (RING - 1);
-        return DIR == 0 ? a * RING + (s ^ ((a & 1) * (RING / 2))) : s * NA + a;
+        if (DIR == 0) return (a * RING) | ((p + 4 * RING + (a & 1) * (RING / 2)) & (RING - 1));
+        return ((p + 4 * RING) * NA + a) & (RING * NA - 1);
     }
     __device__ static __forceinline__ void split(int it, int X, int& p, int& a) {
         if (DIR == 0) {
