@@ -37,7 +37,8 @@ struct FluxLayout {
     // fields per ring slot: Q 5, metric 3, node flux 5, U^L (then h) 5, U^R 5, viscous node flux 4;
     // FP64 adds the stored unit normals of the node (3) and of its + face (4)
     static constexpr int NF_INV = 23, NF_VISC = 27, NF_NRM = 7;
-    static_assert((NA & (NA - 1)) == 0 && (RING & (RING - 1)) == 0, "power-of-two line count and ring");
+    static_assert((NA & (NA - 1)) == 0 && (TP & (TP - 1)) == 0 && (RING & (RING - 1)) == 0,
+                  "power-of-two line count, chunk and ring");
     // Slot of node p: (p mod RING); DIR 0 rotates odd lines by RING/2 (the
     // XOR of the top slot bit, written as an add inside the mask).  The line
     // base has no bits in common with the slot, so each index is an add and
@@ -46,13 +47,22 @@ struct FluxLayout {
         if (DIR == 0) return (a * RING) | ((p + 4 * RING + (a & 1) * (RING / 2)) & (RING - 1));
         return ((p + 4 * RING) * NA + a) & (RING * NA - 1);
     }
+    // Item it (>= 0) of a step over X nodes of NA lines -> (node, line).
+    // Along xi, X is TP (a power of two) after the first chunk: a shift
+    // then, an integer division only in the first chunk.
     __device__ static __forceinline__ void split(int it, int X, int& p, int& a) {
+        const unsigned u = (unsigned)it;
         if (DIR == 0) {
-            p = it % X;
-            a = it / X;
+            if (X == TP) {
+                p = (int)(u % TP);
+                a = (int)(u / TP);
+            } else {
+                p = (int)(u % (unsigned)X);
+                a = (int)(u / (unsigned)X);
+            }
         } else {
-            a = it % NA;
-            p = it / NA;
+            a = (int)(u % NA);
+            p = (int)(u / NA);
         }
     }
     template <class R, bool VISC>
