@@ -80,8 +80,7 @@ typedef struct {
                              accumulation; FP64 metrics and FP64 state.  The RK stage
                              forms its increment -c dt J A in FP32 (the precision of A)
                              and combines it with Q^n and Q^(k) in FP64 (Eq. (20)); its
-                             FP32 copy of the new state rounds to nearest, with
-                             magnitudes below 2^-126 stored as zero                  */
+                             FP32 copy of the new state rounds to nearest             */
     int scheme;           /* 0: modified AFWENO (characteristic space at the node, shared
                              indicators, Figs. 10-11); 1: the original AFWENO
                              (characteristic space at the face, two WENOs per face,

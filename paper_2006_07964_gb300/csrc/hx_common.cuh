@@ -5,8 +5,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "fpconv.h"
-
 namespace hx {
 
 // ---------------------------------------------------------------------------

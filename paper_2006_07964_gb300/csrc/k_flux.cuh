@@ -382,14 +382,14 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     if constexpr (sizeof(R) == 4) {
                         // Mixed form: the increment -cc dt J A is formed in FP32,
                         // the precision A has; its combination with Q^n and Q^(k)
-                        // is FP64, one or two FMAs per field.  The format
-                        // conversions run on the integer pipe (fpconv.h): the
-                        // hardware ones would take FP64 slots.
-                        const float f =
-                            rk.ccf * hx_f64_to_f32(rk.dtl ? rk.dtl[e] : B.dt) * met[9 * fs + e];
+                        // is FP64, one or two FMAs per field.  (GB300 runs the
+                        // format conversions on its FP64 unit; bit-operation
+                        // conversions on the integer pipe measured slower here,
+                        // as they lengthen this latency-bound epilogue.)
+                        const float f = rk.ccf * (float)(rk.dtl ? rk.dtl[e] : B.dt) * met[9 * fs + e];
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
-                            const double r = hx_f32_to_f64(f * dv[k]);
+                            const double r = (double)(f * dv[k]);
                             qo[k] = fma(rk.ca, rk.Qn[k * fs + e], rk.cb != 0.0 ? fma(rk.cb, rk.Qk[k * fs + e], r) : r);
                         }
                     } else {
@@ -424,7 +424,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         float qv[5];
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
-                            qv[k] = hx_f64_to_f32(qo[k]);
+                            qv[k] = (float)qo[k];
                             rk.Qfout[k * fs + e] = qv[k];
                         }
                         if constexpr (sizeof(R) == 4) {

@@ -156,7 +156,7 @@ __global__ void k_bc_farfield(const NodeItem* __restrict__ items, int n, const D
         float qf[5];
         for (int c = 0; c < 5; ++c) {
             Q[c * fs + e] = qb[c];
-            qf[c] = hx_f64_to_f32(qb[c]);
+            qf[c] = (float)qb[c];
             if (Qf) Qf[c * fs + e] = qf[c];
         }
         if (Qf && primf) {   // the node's FP32 primitives, when the next stage's prep skips the interior

@@ -379,10 +379,10 @@ def test_mixed_ns_steps_track_fp64(name):
 @pytest.mark.parametrize("name", ["tgv24", "ogrid_s8", "rotated_ns"])
 def test_mixed_stage_copy_equals_cuda_cast(name):
     """The mixed form's RK stage writes the FP32 stencil copy of its FP64
-    output with an integer-pipe conversion (fpconv.h).  After two steps, the
-    residual evaluated from that copy equals, bit for bit, the residual from
-    the copy hx_set_state makes of the same FP64 state with CUDA's own
-    conversion; the O-grid adds its wall and far-field nodes."""
+    output (and the far-field kernel of its boundary nodes).  After two
+    steps, the residual evaluated from that copy equals, bit for bit, the
+    residual from the copy hx_set_state makes of the same FP64 state; the
+    O-grid adds its wall and far-field nodes."""
     w = CASES[name]()
     ctx = hx.from_workload(w, precision="mixed")
     nb = len(w.blocks)
