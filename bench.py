@@ -398,6 +398,33 @@ def scheme_report(torch, hx, w, steps, warmup, stream):
     return out
 
 
+ORACLE_REPORT_WORKLOADS = ["vortex32", "tgv128", "shock512", "ogrid", "batch64"]
+
+
+def oracle_report(W, steps=2):
+    """The FP64 oracle as it stands, per workload: whole RK3 steps on all of
+    this host's cores and on one thread (CPU only; no GPU is used)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    out = {"report": "oracle", "steps": steps, "host_threads": threads, "workloads": {}}
+    for name in ORACLE_REPORT_WORKLOADS:
+        desc, make = WORKLOADS[name]
+        w = make(W)
+        oracle.set_threads(threads)
+        P = oracle.from_workload(w)
+        dt, _ = P.dt(0.5)
+        row = {"nodes": w.npts}
+        for label, nt in (("all_cores", threads), ("one_thread", 1)):
+            oracle.set_threads(nt)
+            t0 = time.perf_counter()
+            P.step(steps, dt)
+            el = time.perf_counter() - t0
+            row[label] = {"mpts": w.npts * 3 * steps / el / 1e6, "threads": oracle.max_threads(), "seconds": el}
+        out["workloads"][name] = row
+    oracle.set_threads(threads)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,9 +437,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed 128-thread tiles instead of timing the candidates (reproducible profiles)")
     ap.add_argument("--forms", default="fp64,mixed", help="comma list of fp64, mixed")
-    ap.add_argument("--report", choices=["precision", "batch", "scheme"], default=None,
-                    help="print a precision (mixed vs FP64 errors) or batch (batched vs per-instance) report "
-                         "instead of the benchmark line")
+    ap.add_argument("--report", choices=["precision", "batch", "scheme", "oracle"], default=None,
+                    help="print a precision (mixed vs FP64 errors), batch (batched vs per-instance), scheme "
+                         "(modified vs original AFWENO) or oracle (CPU oracle per workload, all cores and one "
+                         "thread) report instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -427,6 +455,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     from paper_2006_07964_gb300 import workloads as W
     desc, make = WORKLOADS[args.workload]
+
+    if args.report == "oracle":
+        if rank == 0:
+            print(json.dumps(oracle_report(W, max(2, args.steps))))
+        return
 
     if args.impl == "reference":
         if rank != 0:
