@@ -387,11 +387,12 @@ __device__ __forceinline__ void weno_pair(float w0, float w1, float w2, float w3
     const float dL = fmaf(5.0f, p12, p23) + t13, dR = fmaf(5.0f, p23, p12) + t13;
     const float e1 = a1 - a2, e2 = a2 - a3;
     const float A = p23 * e1, B = p12 * e2;
-    const float nL = fmaf(3.0f, A, 5.0f * B), nR = fmaf(3.0f, B, 5.0f * A);
     const float uL2 = fmaf(0.125f, fmaf(3.0f, d32, d21), w2);
     const float uR2 = fmaf(-0.125f, fmaf(3.0f, d21, d32), w2);
-    left = fmaf(nL, __fdividef(0.125f, dL), uL2);
-    right = fmaf(-nR, __fdividef(0.125f, dR), uR2);
+    // the 1/8 of the correction folded into the weights' constants
+    const float nL = fmaf(0.375f, A, 0.625f * B), nR = fmaf(0.375f, B, 0.625f * A);
+    left = fmaf(nL, __fdividef(1.0f, dL), uL2);
+    right = fmaf(-nR, __fdividef(1.0f, dR), uR2);
 }
 
 // FP32: each field on its own (hardware reciprocals are cheap).
@@ -611,9 +612,9 @@ struct CharBasis<float> {
         const R s = W[3] + W[4], t = W[3] - W[4];
         const R as = al * s, act = al * c * t;
         U[0] = Wk + as;
-        U[1] = u * Wk + rho * Cx + as * u + act * kx;
-        U[2] = v * Wk + rho * Cy + as * v + act * ky;
-        U[3] = w * Wk + rho * Cz + as * w + act * kz;
+        U[1] = u * U[0] + (rho * Cx + act * kx);
+        U[2] = v * U[0] + (rho * Cy + act * ky);
+        U[3] = w * U[0] + (rho * Cz + act * kz);
         U[4] = half_uu * Wk + rho * (u * Cx + v * Cy + w * Cz) + as * H + al * cth * t;
     }
 };
