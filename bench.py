@@ -55,7 +55,7 @@ RK_FLOPS = 30   # R = -J A and the three-term combination, five components
 # Another workload, or a kernel changed since the capture, reports null.
 TRAFFIC_TGV128 = {
     ("fp64", "flux_xi"): 531.0e6, ("fp64", "flux_eta"): 642.6e6, ("fp64", "flux_zeta_rk"): 761.2e6,
-    ("mixed", "flux_xi"): 194.6e6, ("mixed", "flux_eta"): 242.0e6, ("mixed", "flux_zeta_rk"): 603.7e6,
+    ("mixed", "flux_xi"): 194.2e6, ("mixed", "flux_eta"): 242.2e6, ("mixed", "flux_zeta_rk"): 603.2e6,
 }
 
 
