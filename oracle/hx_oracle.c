@@ -75,8 +75,13 @@
  *       Navier-Stokes, lambda_v = (Ma/Re) max(4/3, gamma/Pr) (mu/rho)
  *       sum_d (J |m_d|)^2; dt_i is taken from Q^n and held for the three
  *       stages of a step.
- * Parity of the physical-face rules (R9, R10) is unpinned: the paper gives no
- * formulas for them.
+ * The paper gives no formulas for the physical-face rules (R9, R10), so the
+ * readings themselves are not pinned to it.  The wall rule with the closure
+ * next to it is pinned to closed forms of the equations it closes: the decay
+ * of a shear mode between no-slip walls, and an acoustic standing wave
+ * between rigid adiabatic walls, inviscid and damped.  The far-field rule is
+ * pinned by invariants only (free stream is a fixed point; the outgoing and
+ * incoming Riemann invariants).
  */
 #include <math.h>
 #include <stdlib.h>

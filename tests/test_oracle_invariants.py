@@ -438,6 +438,91 @@ def test_heat_conduction_decay_rate():
     assert amp / A == pytest.approx(np.exp(-alpha * Tend), rel=0.02)
 
 
+# ---------------------------------------------------------------- walls (reading R10) against closed forms
+
+def _channel(nj, q, **kw):
+    """8 x nj x 8 lattice: x and z periodic (unit periods), no-slip adiabatic
+    walls at y = 0 and y = pi, the boundary nodes on the walls."""
+    ni = nk = 8
+    H = np.pi
+    x, y, z = np.arange(ni) / ni, np.arange(nj) * H / (nj - 1), np.arange(nk) / nk
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    P = oracle.Problem(gamma=G, **kw)
+    P.add_block(np.stack([X, Y, Z]))
+    P.set_face(0, 0, "periodic", 0, 1, (-1.0, 0.0, 0.0))
+    P.set_face(0, 1, "periodic", 0, 0, (1.0, 0.0, 0.0))
+    P.set_face(0, 2, "wall")
+    P.set_face(0, 3, "wall")
+    P.set_face(0, 4, "periodic", 0, 5, (0.0, 0.0, -1.0))
+    P.set_face(0, 5, "periodic", 0, 4, (0.0, 0.0, 1.0))
+    P.check()
+    P.metrics()
+    P.set_state(0, q)
+    return P
+
+
+def _channel_y(nj):
+    return np.broadcast_to((np.arange(nj) * np.pi / (nj - 1))[None, :, None], (8, nj, 8))
+
+
+def _mode(f, shape_fn):
+    return (f * shape_fn).sum() / (shape_fn * shape_fn).sum()
+
+
+def test_no_slip_channel_shear_decay():
+    """u = A sin(y) between no-slip walls at y = 0, pi, rho = 1, p uniform:
+    the Euler terms vanish (a parallel flow) and the mode decays as
+    exp(-nu t), nu = (Ma/Re) mu / rho (mu = 1).  This exercises the wall
+    node's velocity and the wall mirror of the tangential velocity (the
+    upwind flux sees it), and the viscous closure next to the wall."""
+    nj, A = 33, 1e-3
+    Y = _channel_y(nj)
+    s = np.sin(Y)
+    q = W.conservative(G, np.ones_like(s), A * s, 0.0, 0.0, 1.0 / G)
+    mach, re = 0.5, 5.0
+    P = _channel(nj, q, mach=mach, reynolds=re, viscous=True, mu_law=0)
+    T, ns = 1.0, 40
+    P.step(ns, T / ns)
+    amp = _mode(P.get_state(0)[1], s)
+    assert amp / A == pytest.approx(np.exp(-mach / re * T), rel=5e-5)
+
+
+def test_acoustic_standing_wave_between_walls():
+    """Linear acoustics between rigid walls at y = 0, pi: p' = eps cos(y),
+    rho' = p' (c = 1), at rest, is a standing wave of angular frequency 1;
+    after half a period, t = pi, p' = -eps cos(y).  Euler; this exercises the
+    wall mirror of the normal velocity."""
+    nj, eps = 33, 1e-4
+    c = np.cos(_channel_y(nj))
+    q = W.conservative(G, 1.0 + eps * c, 0.0, 0.0, 0.0, 1.0 / G + eps * c)
+    P = _channel(nj, q, mach=0.5, reynolds=1e6, viscous=False)
+    ns = 80
+    P.step(ns, np.pi / ns)
+    r, u, v, w, p = W.primitive(G, P.get_state(0))
+    assert _mode(p - 1.0 / G, c) / eps == pytest.approx(-1.0, rel=1e-4)
+
+
+def test_acoustic_damping_between_adiabatic_walls():
+    """The same standing wave with viscosity and heat conduction: a plane
+    mode between rigid adiabatic walls has no boundary layer and decays at
+    the classical (Stokes-Kirchhoff) rate delta = k^2/2 (4/3 nu + (gamma-1)
+    nu/Pr), k = 1; at t = pi, p' = -eps exp(-delta pi) cos(y).  The
+    leading-order rate leaves a relative error of order (delta/omega)^2,
+    7e-5 here.  This exercises the wall node's normal velocity under the
+    viscous normal stress."""
+    nj, eps = 33, 1e-4
+    c = np.cos(_channel_y(nj))
+    q = W.conservative(G, 1.0 + eps * c, 0.0, 0.0, 0.0, 1.0 / G + eps * c)
+    mach, re, pr = 0.5, 10.0, 0.71
+    P = _channel(nj, q, mach=mach, reynolds=re, prandtl=pr, viscous=True, mu_law=0)
+    ns = 80
+    P.step(ns, np.pi / ns)
+    r, u, v, w, p = W.primitive(G, P.get_state(0))
+    nu = mach / re
+    delta = 0.5 * (4.0 / 3.0 * nu + (G - 1.0) * nu / pr)
+    assert _mode(p - 1.0 / G, c) / eps == pytest.approx(-np.exp(-delta * np.pi), rel=3e-4)
+
+
 def test_tgv_viscous_dissipation_rate():
     """Taylor-Green vortex at t = 0: the viscous part of dK/dt equals
     -2 nu |k|^2 K = -6 nu K for its |k|^2 = 3 modes (within the Ma = 0.1

@@ -45,6 +45,10 @@ MUTANTS = [
     ("local dt viscous factor", "(gp > 4.0 / 3.0 ? gp : 4.0 / 3.0)", "4.0 / 3.0"),
     ("local dt block", "const double h = dtl ? dtl[b][t % N] : dt[b];", "const double h = dtl ? dtl[0][t % N] : dt[b];"),
     ("face flux pairing", "qr[c] = UR[c * L + f + 1 + O];", "qr[c] = UR[c * L + f + O];"),
+    ("wall node tangential velocity kept", "Qs[b][1 * N + p] = 0.0;", "(void)0;"),
+    ("wall node normal velocity kept", "Qs[b][2 * N + p] = 0.0;", "(void)0;"),
+    ("wall mirror tangential even", "        q[1] = -q[1];", "        q[1] = q[1];"),
+    ("wall mirror normal even", "        q[2] = -q[2];", "        q[2] = q[2];"),
 ]
 
 
