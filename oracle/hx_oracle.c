@@ -80,8 +80,10 @@
  * next to it is pinned to closed forms of the equations it closes: the decay
  * of a shear mode between no-slip walls, and an acoustic standing wave
  * between rigid adiabatic walls, inviscid and damped.  The far-field rule is
- * pinned by invariants only (free stream is a fixed point; the outgoing and
- * incoming Riemann invariants).
+ * pinned by its invariants (free stream is a fixed point; the outgoing and
+ * incoming Riemann invariants) and by the property that defines a
+ * characteristic boundary: a plane acoustic pulse leaves through it, at the
+ * outflow or the inflow end, without reflection.
  */
 #include <math.h>
 #include <stdlib.h>

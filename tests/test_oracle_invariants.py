@@ -523,6 +523,48 @@ def test_acoustic_damping_between_adiabatic_walls():
     assert _mode(p - 1.0 / G, c) / eps == pytest.approx(-np.exp(-delta * np.pi), rel=3e-4)
 
 
+def _duct(ni, q, mach):
+    """ni x 8 x 8 lattice over x in [0, 10] with far-field faces at both ends
+    (free stream Ma along +x), y and z periodic (unit periods)."""
+    x, y, z = np.arange(ni) * 10.0 / (ni - 1), np.arange(8) / 8.0, np.arange(8) / 8.0
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    P = oracle.Problem(gamma=G, mach=mach, reynolds=1e6, viscous=False)
+    P.add_block(np.stack([X, Y, Z]))
+    P.set_face(0, 0, "farfield")
+    P.set_face(0, 1, "farfield")
+    P.set_face(0, 2, "periodic", 0, 3, (0.0, -1.0, 0.0))
+    P.set_face(0, 3, "periodic", 0, 2, (0.0, 1.0, 0.0))
+    P.set_face(0, 4, "periodic", 0, 5, (0.0, 0.0, -1.0))
+    P.set_face(0, 5, "periodic", 0, 4, (0.0, 0.0, 1.0))
+    P.check()
+    P.metrics()
+    P.set_state(0, q)
+    return P
+
+
+@pytest.mark.parametrize("direction", [+1, -1], ids=["out_downstream", "out_upstream"])
+def test_farfield_lets_an_acoustic_pulse_out(direction):
+    """A plane acoustic pulse (a simple wave: p' = rho' = eps g, u' = +-eps g
+    for c = 1) runs at Ma +- 1 through the free stream and leaves through a
+    far-field face: downstream (outflow) or upstream (inflow).  A
+    characteristic boundary reflects nothing of a plane wave at normal
+    incidence, so once the pulse has left, the domain is back at the free
+    stream: the largest remaining |p'| and |u'| are below 2 % of eps (about
+    1 % measured, from the boundary node's one-sided treatment).  A
+    reflecting boundary leaves an order-one fraction."""
+    ni, mach, eps = 81, 0.2, 1e-4
+    X = np.broadcast_to((np.arange(ni) * 10.0 / (ni - 1))[None, None, :], (8, 8, ni))
+    g = np.exp(-((X - 5.0) / 0.6) ** 2)
+    q = W.conservative(G, 1.0 + eps * g, mach + direction * eps * g, 0.0, 0.0, 1.0 / G + eps * g)
+    P = _duct(ni, q, mach)
+    tend = 8.0 / (1.0 + direction * mach)
+    ns = int(np.ceil(tend / (0.4 * 10.0 / (ni - 1) / (1.0 + mach))))
+    P.step(ns, tend / ns)
+    r, u, v, w, p = W.primitive(G, P.get_state(0))
+    assert np.abs(p - 1.0 / G).max() < 0.02 * eps
+    assert np.abs(u - mach).max() < 0.02 * eps
+
+
 def test_tgv_viscous_dissipation_rate():
     """Taylor-Green vortex at t = 0: the viscous part of dK/dt equals
     -2 nu |k|^2 K = -6 nu K for its |k|^2 = 3 modes (within the Ma = 0.1

@@ -49,6 +49,9 @@ MUTANTS = [
     ("wall node normal velocity kept", "Qs[b][2 * N + p] = 0.0;", "(void)0;"),
     ("wall mirror tangential even", "        q[1] = -q[1];", "        q[1] = q[1];"),
     ("wall mirror normal even", "        q[2] = -q[2];", "        q[2] = q[2];"),
+    ("far-field outgoing from free stream", "double Rp = uni + 2.0 * s.c / (g - 1.0);",
+     "double Rp = unf + 2.0 * cinf / (g - 1.0);"),
+    ("far-field entropy side", "    if (un > 0.0) {\n        ent = s.p", "    if (un < 0.0) {\n        ent = s.p"),
 ]
 
 
