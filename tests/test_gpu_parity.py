@@ -84,6 +84,47 @@ def rotated(w, parts, perms):
     return ws
 
 
+def channel(dims=(24, 25, 16), viscous=True, reynolds=50.0):
+    """Walls at y = 0 and pi (j faces), x and z periodic; a 3D perturbed
+    shear flow, so that every term is active next to the walls."""
+    ni, nj, nk = dims
+    Lx, H, Lz = 4.0, np.pi, 2.0
+    x, y, z = np.arange(ni) * Lx / ni, np.arange(nj) * H / (nj - 1), np.arange(nk) * Lz / nk
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    xyz = np.stack([X, Y, Z])
+    kx, kz = 2 * np.pi / Lx, 2 * np.pi / Lz
+    u = 0.3 * np.sin(Y) * (1 + 0.2 * np.cos(kx * X) * np.cos(kz * Z))
+    v = 0.05 * np.sin(Y) ** 2 * np.sin(kx * X)
+    w = 0.05 * np.sin(Y) * np.sin(kz * Z)
+    rho = 1.0 + 0.05 * np.cos(kx * X) * np.cos(Y)
+    q = W.conservative(1.4, rho, u, v, w, 1.0 / 1.4 * (1.0 + 0.05 * np.sin(kz * Z) * np.cos(Y)))
+    faces = [W.Face("periodic", 0, 1, (-Lx, 0.0, 0.0)), W.Face("periodic", 0, 0, (Lx, 0.0, 0.0)),
+             W.Face("wall"), W.Face("wall"),
+             W.Face("periodic", 0, 5, (0.0, 0.0, -Lz)), W.Face("periodic", 0, 4, (0.0, 0.0, Lz))]
+    return W.Workload("channel", [W.Block(xyz, faces, q)], gamma=1.4, mach=0.5, reynolds=reynolds,
+                      viscous=viscous, mu_law=1)
+
+
+def duct(dims=(41, 12, 10), viscous=False):
+    """Far field at both x ends (i faces, the unit-stride sweep), y and z
+    periodic; two pressure pulses with transverse variation next to the two
+    ends, so that waves leave through the inflow and the outflow face."""
+    ni, nj, nk = dims
+    Lx, Ly, Lz = 10.0, 2.0, 2.0
+    x, y, z = np.arange(ni) * Lx / (ni - 1), np.arange(nj) * Ly / nj, np.arange(nk) * Lz / nk
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    xyz = np.stack([X, Y, Z])
+    g = (np.exp(-((X - 1.5) / 0.8) ** 2) + np.exp(-((X - 8.5) / 0.8) ** 2)) * \
+        (1 + 0.3 * np.sin(np.pi * Y) * np.cos(np.pi * Z))
+    eps, mach = 0.02, 0.2
+    q = W.conservative(1.4, 1.0 + eps * g, mach, 0.01 * g, 0.0, 1.0 / 1.4 + eps * g)
+    faces = [W.Face("farfield"), W.Face("farfield"),
+             W.Face("periodic", 0, 3, (0.0, -Ly, 0.0)), W.Face("periodic", 0, 2, (0.0, Ly, 0.0)),
+             W.Face("periodic", 0, 5, (0.0, 0.0, -Lz)), W.Face("periodic", 0, 4, (0.0, 0.0, Lz))]
+    return W.Workload("duct", [W.Block(xyz, faces, q)], gamma=1.4, mach=mach, reynolds=100.0,
+                      viscous=viscous, mu_law=1)
+
+
 CASES = {
     "vortex32": lambda: W.vortex(32),
     "ragged_euler": lambda: warped((37, 29, 23)),
@@ -98,6 +139,9 @@ CASES = {
     "rotated_euler": lambda: rotated(warped((28, 24, 20)), (2, 2, 1), {1: (3, 1, 2), 2: (-1, -2, 3), 3: (1, -3, 2)}),
     "rotated_ns": lambda: rotated(warped((24, 22, 26), viscous=True, reynolds=100.0), (1, 1, 2),
                                   {0: (-2, 1, 3), 1: (2, 3, 1)}),
+    "channel_ns": lambda: channel(),
+    "duct_euler": lambda: duct(),
+    "duct_ns": lambda: duct(viscous=True),
 }
 
 
@@ -153,7 +197,8 @@ def test_free_stream_residual_gpu():
 
 @pytest.mark.parametrize("name,steps", [("vortex32", 10), ("ragged_euler", 4), ("tgv24", 5), ("split_ns", 3),
                                         ("ogrid_s4", 5), ("shock_warped", 20), ("rotated_euler", 4),
-                                        ("rotated_ns", 3), ("tiny_ns3", 4), ("min6", 4)])
+                                        ("rotated_ns", 3), ("tiny_ns3", 4), ("min6", 4), ("channel_ns", 5),
+                                        ("duct_euler", 10), ("duct_ns", 5)])
 def test_steps_parity(name, steps):
     w, ctx, P = pair(name)
     dt, _ = P.dt(0.5)
