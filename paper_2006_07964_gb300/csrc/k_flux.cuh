@@ -5,7 +5,9 @@
 // over a list of line groups) and marches along them in chunks of TP nodes,
 // keeping a ring of RING nodes per line in shared memory.  Every node's
 // work is done once; per chunk c (nodes c*TP ..):
-//   load  state and metric of d at nodes c*TP+3 .. c*TP+TP+2;
+//   load  state and metric of d at nodes c*TP+3 .. c*TP+TP+2 (FP64: and the
+//         stored unit normals); FP32: L2 prefetch hints for this chunk's
+//         output step and the next chunk's load and node steps;
 //   node  at nodes c*TP+1 .. c*TP+TP: characteristic projection of the
 //         5-node stencil at the node (modified AFWENO, Sec. 4.5.1,
 //         Figs. 10-11), WENO5 left value at the node's + face and right
@@ -73,7 +75,9 @@ struct FluxLayout {
 
 // RK (last sweep only): instead of storing A, finish R = -J (A + div) and
 // the RK3 stage combination at each output node (Eq. (20), FP64), with the
-// wall-node values and the non-finite / non-physical flags.
+// wall-node values and the non-finite / non-physical flags; the mixed form
+// also writes the FP32 copy of the stage output and, when asked
+// (rk.primout), its primitives for the next stage.
 // SCH 0: modified AFWENO (characteristic space at the node, Figs. 10-11);
 // SCH 1: original AFWENO (characteristic space at the face from the mean
 // state and the face metric, two independent WENOs per face, Fig. 9).
