@@ -55,7 +55,9 @@
  *       along the outward normal of the boundary node, outgoing invariant from
  *       the node next to it, incoming from the free stream; entropy and
  *       tangential velocity upwinded by the sign of the normal velocity.
- *   R11 viscosity: mu = 1 or Sutherland T^(3/2)(1+S)/(T+S).
+ *   R11 viscosity: mu = 1 or Sutherland T^(3/2)(1+S)/(T+S), temperatures in
+ *       units of the free stream (pinned to the viscosity ratios that the
+ *       U.S. Standard Atmosphere 1976 tabulates).
  *   R12 tau and q carry the factor Ma/Re; q = Ma mu/(Re Pr (gamma-1)) dT/dx_j.
  *   R13 original AFWENO (Fig. 9): the characteristic space of face i+1/2 is
  *       built from the arithmetic mean of Q_i and Q_{i+1} and the unit normal

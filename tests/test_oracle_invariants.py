@@ -414,6 +414,34 @@ def test_shear_wave_decay_rate():
     assert amp / A == pytest.approx(np.exp(-nu * T), rel=2e-3)
 
 
+def test_shear_wave_decay_rate_sutherland():
+    """The shear wave of the test above at a uniform temperature of
+    216.65 K / 288.15 K with Sutherland's law (reading R11): it decays as
+    exp(-nu t) with nu = (Ma/Re) mu(T)/rho, and mu(T) is the ratio the U.S.
+    Standard Atmosphere 1976 tabulates for those two temperatures
+    (tests/golden), not a value the oracle computes."""
+    from golden_data import air_viscosity_table
+    table = dict(air_viscosity_table())
+    T = 216.65 / 288.15
+    mu = table[216.65] / table[288.15]
+    n = 16
+    L = 2 * np.pi
+    xyz = W.warped_box((n, n, n), (L, L, L), 0.02)
+    A = 1e-3
+    u = A * np.sin(xyz[1])
+    rho = 1.0 / T   # p = 1/gamma, T = gamma p / rho
+    q = W.conservative(G, np.full_like(u, rho), u, 0.0, 0.0, 1.0 / G)
+    mach, re = 0.5, 1.0
+    P = _single(xyz, q, (L, L, L), mach=mach, reynolds=re, viscous=True, mu_law=1)
+    nu = mach / re * mu / rho
+    Tend, ns = 2.0, 40
+    P.step(ns, Tend / ns)
+    qq = P.get_state(0)
+    amp = (qq[1] * np.sin(xyz[1])).sum() / (np.sin(xyz[1]) ** 2).sum() / rho
+    rate = -np.log(amp / A) / Tend
+    assert rate == pytest.approx(nu, rel=1e-3)   # measured 3e-4 (time and space truncation)
+
+
 def test_heat_conduction_decay_rate():
     """Entropy wave T = 1 + A sin(y) at uniform p, at rest: in the isobaric
     limit T decays as exp(-alpha t), alpha = (Ma/Re) mu/(Pr rho) (c_p = 1/(gamma-1))."""

@@ -51,6 +51,9 @@ MUTANTS = [
     ("wall mirror normal even", "        q[2] = -q[2];", "        q[2] = q[2];"),
     ("far-field outgoing from free stream", "double Rp = uni + 2.0 * s.c / (g - 1.0);",
      "double Rp = unf + 2.0 * cinf / (g - 1.0);"),
+    ("sutherland exponent", "return T * sqrt(T) * (1.0 + S) / (T + S);", "return T * (1.0 + S) / (T + S);"),
+    ("sutherland sign of S", "return T * sqrt(T) * (1.0 + S) / (T + S);", "return T * sqrt(T) * (1.0 + S) / (T - S);"),
+    ("sutherland normalisation", "return T * sqrt(T) * (1.0 + S) / (T + S);", "return T * sqrt(T) * S / (T + S);"),
     ("far-field entropy side", "    if (un > 0.0) {\n        ent = s.p", "    if (un < 0.0) {\n        ent = s.p"),
 ]
 

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from golden_data import coefficients
+from golden_data import air_viscosity_table, coefficients
 
 pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
 RNG = np.random.default_rng(12345)
@@ -320,3 +320,46 @@ def test_viscous_stress_vanishes_for_rigid_rotation():
     g = np.concatenate([grad_u.ravel(), np.zeros(3)])
     tau, beta = _stress_rows(ops, q, g)
     assert np.abs(tau).max() < 1e-15 and np.abs(beta).max() < 1e-15
+
+
+# ---------------------------------------------------------------- Sutherland's law (reading R11)
+
+T_INF_K = 288.15   # free-stream temperature in kelvin: the sea-level row of the table, the solver's unit
+
+
+def _mu(ops, T, mach=0.7, reynolds=13.0):
+    """The oracle's viscosity at temperature T (free-stream units), read
+    through its viscous flux: with du/dy = 1 the only gradient,
+    tau_xy = (Ma/Re) mu, the x-momentum entry of the flux along (0, 1, 0)."""
+    q = cons(1.0, 0.1, -0.2, 0.05, T / G)   # rho = 1, T = gamma p / rho
+    g = np.zeros(12)
+    g[1] = 1.0
+    fv = ops.viscous_flux(q, g, np.array([0.0, 1.0, 0.0]))
+    return fv[1] / (mach / reynolds)
+
+
+def test_sutherland_is_one_at_the_free_stream_temperature():
+    """The Reynolds number is formed with the free-stream viscosity, so
+    mu(T = 1) = 1 (Eq. (1) definitions)."""
+    ops = oracle.Ops(gamma=G, mach=0.7, reynolds=13.0, viscous=True, mu_law=1)
+    assert _mu(ops, 1.0) == pytest.approx(1.0, rel=1e-15)
+
+
+def test_sutherland_reproduces_the_standard_atmosphere_table():
+    """Reading R11 (the paper leaves mu(T) open): Sutherland's law with
+    S = 110.4 K / 288.15 K.  Its values must reproduce the viscosity ratios
+    the U.S. Standard Atmosphere 1976 tabulates (five significant digits, so
+    1.5e-4 relative), which a wrong exponent or a wrong sign of S misses by
+    percents."""
+    ops = oracle.Ops(gamma=G, mach=0.7, reynolds=13.0, viscous=True, mu_law=1)
+    rows = air_viscosity_table()
+    ref = dict(rows)[T_INF_K]
+    assert len(rows) >= 2
+    for T_k, mu_k in rows:
+        assert _mu(ops, T_k / T_INF_K) == pytest.approx(mu_k / ref, rel=1.5e-4), T_k
+
+
+def test_constant_viscosity_law_ignores_temperature():
+    ops = oracle.Ops(gamma=G, mach=0.7, reynolds=13.0, viscous=True, mu_law=0)
+    for T in (0.5, 1.0, 2.5):
+        assert _mu(ops, T) == pytest.approx(1.0, rel=1e-15)
