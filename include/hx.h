@@ -254,6 +254,9 @@ size_t hx_device_bytes(const hx_ctx* ctx);
  *   met    device [10][nk][nj][ni] node metrics and J, as hx_get_metrics
  *          returns them for that periodic block
  *   r_out  device [5][nk][nj][ni], written
+ * q, met and r_out must be memory of the current device (device or managed
+ * allocations); host memory or another GPU's memory is rejected with
+ * HX_ERR_INVALID_ARG.
  * The result equals hx_rhs of an FP64 Euler context holding that block with
  * periodic faces, up to rounding.  All intermediates live in one static
  * device array of 32 MiB that the library holds on every GPU it is loaded

@@ -1,4 +1,5 @@
-"""Builds libhx.so in-tree from csrc/*.cu with nvcc for sm_103a.
+"""Builds libhx.so in-tree from csrc/*.cu with nvcc for sm_103a (and
+libhx_probe.so, the benchmark's FMA peak probe, from probe/alu_peaks.cu).
 
 Translation units compile in parallel; the shared library links the CUDA
 runtime statically.  Rebuilds only when a source or header is newer than the
@@ -18,6 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "hx")
 LIB = os.path.join(HERE, "libhx.so")
 LIB_CHECKED = os.path.join(HERE, "libhx_checked.so")
+# the benchmark's measurement support (FP64 / FP32 FMA peaks), include/hx_probe.h
+PROBE_SRC = os.path.join(HERE, "probe", "alu_peaks.cu")
+LIB_PROBE = os.path.join(HERE, "libhx_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -45,7 +49,23 @@ def stale(lib=LIB):
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
+def build_probe(force=False):
+    """libhx_probe.so: the FMA peak probe of include/hx_probe.h."""
+    if not force and os.path.exists(LIB_PROBE) and os.path.getmtime(LIB_PROBE) >= max(
+            os.path.getmtime(PROBE_SRC), os.path.getmtime(os.path.join(INCLUDE, "hx_probe.h"))):
+        return LIB_PROBE
+    tmp = LIB_PROBE + ".tmp%d" % os.getpid()
+    cmd = [_nvcc()] + FLAGS + ARCH + ["-shared", "-o", tmp, PROBE_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s%s" % (PROBE_SRC, r.stdout, r.stderr))
+    os.replace(tmp, LIB_PROBE)
+    return LIB_PROBE
+
+
 def build(force=False, verbose=False, ptxas_info=False, checked=False):
+    if not checked:
+        build_probe(force)
     lib = LIB_CHECKED if checked else LIB
     bdir = BUILD + "_checked" if checked else BUILD
     if not force and not stale(lib):

@@ -21,9 +21,11 @@ constexpr size_t kScratchBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // In host code g_scratch names a host-side stand-in, not device memory: the
-// device address is looked up once per device with cudaGetSymbolAddress.
+// device address is looked up once per device with cudaGetSymbolAddress,
+// together with the device's SM count (the persistent grids' size).
 std::mutex g_mu;
 std::vector<void*> g_addr;
+std::vector<int> g_sms;
 
 constexpr int kNA = 16, kVariant = 1;   // flux variant 1: 16 nodes per chunk x 16 lines, every direction
 
@@ -78,21 +80,38 @@ __global__ void k_na_out(DevBlock B, long long fs, const double* __restrict__ A,
     }
 }
 
-int scratch_address(void** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return HX_ERR_CUDA;
+int scratch_address(int dev, void** out, int* sms) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if ((int)g_addr.size() <= dev) g_addr.resize(dev + 1, nullptr);
+    if ((int)g_addr.size() <= dev) {
+        g_addr.resize(dev + 1, nullptr);
+        g_sms.resize(dev + 1, 0);
+    }
     if (!g_addr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+        int n = 0;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
             cudaGetLastError();
             return HX_ERR_CUDA;
         }
         g_addr[dev] = p;
+        g_sms[dev] = n;
     }
     *out = g_addr[dev];
+    *sms = g_sms[dev];
     return HX_OK;
+}
+
+// A caller's array must be device (or managed) memory of the current
+// device: a pointer to another GPU's memory, or to host memory, would be
+// dereferenced by the kernels without peer access.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -122,8 +141,12 @@ extern "C" int hx_euler_rhs_periodic_noalloc(int ni, int nj, int nk, double gamm
     const size_t need = off_a + 5 * (size_t)fs * 8;
     if (need > kScratchBytes) return HX_ERR_INVALID_ARG;   // grid larger than the static scratch
 
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HX_ERR_CUDA;
+    if (!on_device(q, dev) || !on_device(met, dev) || !on_device(r_out, dev)) return HX_ERR_INVALID_ARG;
     unsigned char* base = nullptr;
-    int rc = scratch_address((void**)&base);
+    int sms = 0;
+    int rc = scratch_address(dev, (void**)&base, &sms);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     DevBlock* dB = (DevBlock*)base;
@@ -152,7 +175,7 @@ extern "C" int hx_euler_rhs_periodic_noalloc(int ni, int nj, int nk, double gamm
         // sets the kernel's shared-memory opt-in (no allocation) and sizes the grid
         const int cps = flux_ctas_per_sm(true, d, kVariant, false);
         if (cps <= 0) return HX_ERR_CUDA;
-        a.grid = nd[d] < 152 * cps ? nd[d] : 152 * cps;
+        a.grid = nd[d] < sms * cps ? nd[d] : sms * cps;
         if (launch_flux(true, d, kVariant, false, a, s) != cudaSuccess) return HX_ERR_CUDA;
     }
     k_na_out<<<1024, 256, 0, s>>>(B, fs, A, met, r_out);

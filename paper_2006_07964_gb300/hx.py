@@ -108,12 +108,18 @@ def load(path=None):
 
 
 def _ptr(a, nvals=None):
-    """(address, on_device) of a numpy array or a CUDA tensor."""
+    """(address, on_device) of a numpy array or a CUDA tensor.  A CUDA
+    tensor's producers on torch's current stream of its device are waited
+    for first: the library works on its own stream, which is not ordered
+    after torch's."""
     if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
         if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
             raise ValueError("device tensors must be contiguous float64")
         if nvals is not None and a.numel() != nvals:
             raise ValueError("expected %d values, got %d" % (nvals, a.numel()))
+        if a.is_cuda:
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
         return a.data_ptr(), int(bool(a.is_cuda))
     if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
         raise ValueError("host arrays must be C-contiguous float64 numpy arrays")
@@ -300,17 +306,26 @@ def euler_rhs_periodic_noalloc(q, met, r_out, gamma=1.4, stream=None):
     """Residual of one fully periodic Euler block in FP64 without any device
     allocation (hx_euler_rhs_periodic_noalloc); q [5][nk][nj][ni], met
     [10][nk][nj][ni] and r_out [5][nk][nj][ni] are contiguous float64 CUDA
-    tensors.  For callers that cannot allocate device memory; see
-    include/hx.h for the size limit and the shared-scratch caveat."""
+    tensors on one device, which the call makes current.  stream: a
+    cudaStream_t handle, default torch's current stream of that device, so
+    that the call is ordered after the tensors' producers.  For callers that
+    cannot allocate device memory; see include/hx.h for the size limit and
+    the shared-scratch caveat."""
+    import torch
     for t in (q, met, r_out):
         if not (hasattr(t, "is_cuda") and t.is_cuda):
             raise ValueError("q, met and r_out must be CUDA tensors")
+    if not (q.device == met.device == r_out.device):
+        raise ValueError("q, met and r_out must be on one device")
     _, nk, nj, ni = q.shape
-    _ptr(q, 5 * nk * nj * ni)
-    _ptr(met, 10 * nk * nj * ni)
-    _ptr(r_out, 5 * nk * nj * ni)
-    rc = load().hx_euler_rhs_periodic_noalloc(ni, nj, nk, float(gamma), q.data_ptr(), met.data_ptr(),
-                                              r_out.data_ptr(), ctypes.c_void_p(stream or 0))
+    for t, nf in ((q, 5), (met, 10), (r_out, 5)):
+        if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != nf * nk * nj * ni:
+            raise ValueError("expected a contiguous float64 tensor of %d values" % (nf * nk * nj * ni))
+    with torch.cuda.device(q.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(q.device).cuda_stream
+        rc = load().hx_euler_rhs_periodic_noalloc(ni, nj, nk, float(gamma), q.data_ptr(), met.data_ptr(),
+                                                  r_out.data_ptr(), ctypes.c_void_p(stream or 0))
     if rc:
         raise HxError(rc, "hx_euler_rhs_periodic_noalloc failed")
     return r_out
@@ -332,3 +347,22 @@ def from_workload(w, precision="fp64", stream=None, autotune=1, mem_cap_bytes=0,
     for b, blk in enumerate(w.blocks):
         ctx.set_state(b, blk.q0)
     return ctx
+
+
+PROBE_PATH = os.path.join(HERE, "libhx_probe.so")
+PROBE_EXPORTS = ("hx_probe_fma_peaks",)   # include/hx_probe.h
+
+
+def probe_fma_peaks():
+    """Measured (fp64_tflops, fp32_tflops) of the current GPU from
+    libhx_probe.so (include/hx_probe.h): the FMA-chain probe the benchmark's
+    ALU roofline divides by."""
+    lib = ctypes.CDLL(PROBE_PATH)
+    fn = lib.hx_probe_fma_peaks
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3
+    f64, f32, ms = ctypes.c_double(), ctypes.c_double(), (ctypes.c_double * 2)()
+    rc = fn(ctypes.byref(f64), ctypes.byref(f32), ms)
+    if rc:
+        raise HxError(rc, "hx_probe_fma_peaks failed")
+    return f64.value, f32.value

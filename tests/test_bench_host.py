@@ -1,6 +1,6 @@
 """Host-side logic of bench.py on the CPU: the oracle timing modes (all
-cores and one thread) and the algorithmic byte model of the fused RK sweep
-that the roofline figure divides by."""
+cores and one thread), the algorithmic byte model of an RK stage that the
+roofline figure divides by, and the traffic table's source check."""
 import pytest
 
 import bench
@@ -21,21 +21,51 @@ def test_oracle_report_times_all_cores_and_one_thread(monkeypatch):
         assert r["mpts"] == pytest.approx(row["nodes"] * 3 * 2 / r["seconds"] / 1e6)
 
 
-def test_cpu_baseline_adds_the_single_thread_figure():
-    out = bench.cpu_baseline(W.vortex(16), seconds_target=0.2)
+def test_cpu_baseline_times_two_whole_steps_on_all_cores_and_one_thread():
+    out = bench.cpu_baseline(W.vortex(16), steps=2, single_thread_w=W.vortex(12))
     assert out["kind"] == "oracle" and out["unit"] == "Mpts/s" and out["value"] > 0
+    assert out["sample"].startswith("2 full RK3 steps of the 4096-node workload")
     st = out["single_thread"]
     assert st["cores"] == 1 and st["value"] > 0 and st["unit"] == "Mpts/s"
+    assert st["sample"].startswith("2 full RK3 steps of vortex12 (1728 nodes)")
 
 
-def test_rk_sweep_byte_model():
-    """Per node, averaged over the three stages as the launch time is.
-    FP64: A read instead of read + write (-5 words), Q^n, J, Q^(k+1) (+11).
-    Mixed: -5 FP32 words; Q^n, Q^(k+1) and, in two stages of three, Q^(k)
-    in FP64; J, the FP32 copy and A_ref in FP32; for Navier-Stokes the FP32
-    primitives of the output in two stages of three."""
-    assert bench.rk_extra_bytes_per_node("fp64", False) == -5 * 8 + 11 * 8
-    assert bench.rk_extra_bytes_per_node("fp64", True) == bench.rk_extra_bytes_per_node("fp64", False)
-    euler = -5 * 4 + (5 + 5 * 2 / 3 + 5) * 8 + 4 + 5 * 4 + 5 * 4
-    assert bench.rk_extra_bytes_per_node("mixed", False) == pytest.approx(euler)
-    assert bench.rk_extra_bytes_per_node("mixed", True) == pytest.approx(euler + 16 * 2 / 3)
+def test_stage_byte_model_is_the_compulsory_traffic():
+    """Per node and RK stage, the compulsory HBM traffic of Eq. (20) with
+    FP64 metrics: stage 1 reads the 9 metrics and J and Q^n and writes
+    Q^(1) (20 words = 160 B); stages 2 and 3 also read their input Q^(k)
+    (25 words = 200 B); the mixed form adds an FP32 copy of the state read
+    and written (10 x 4 B), 240 B in stages 2 and 3."""
+    assert bench.stage_bytes_per_node("fp64") == pytest.approx((160 + 200 + 200) / 3)
+    assert bench.stage_bytes_per_node("mixed") == pytest.approx((200 + 240 + 240) / 3)
+
+
+def test_traffic_is_null_unless_the_sources_match(monkeypatch):
+    """The roofline's DRAM traffic comes from an ncu capture keyed by the
+    kernel sources' hash; another hash reports null."""
+    sha = bench.kernel_sources_sha()
+    assert len(sha) == 16 and sha == bench.kernel_sources_sha()
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA", "0" * 16)
+    monkeypatch.setattr(bench, "TRAFFIC_PER_NODE", {("fp64", "flux_xi"): 100.0})
+
+    class Ctx:
+        def profile_step(self, steps, dt):
+            return {"flux_xi": (6, 6.0), "prep": (6, 1.0)}
+
+        def tuning(self):
+            return {}
+
+    class Wl:
+        npts = 1000
+        viscous = True
+
+    peaks = {"hbm_gbs": 6800.0, "src": "fallback", "fp64_tflops": 1.0, "fp32_tflops": 64.0, "alu_src": "x"}
+    out = bench.roofline_for(Ctx(), Wl(), "fp64", 2, 1e-3, peaks, 9.0)
+    assert out["traffic"] is None and out["bound"] == "alu"
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA", sha)
+    out = bench.roofline_for(Ctx(), Wl(), "fp64", 2, 1e-3, peaks, 9.0)
+    assert out["traffic"] == pytest.approx(100.0 * 1000)
+    # achieved flops per launch over the launch time (1 ms)
+    flops = (bench.FLUX_FLOPS_INV + bench.FLUX_FLOPS_VISC - bench.FLUX_FLOPS_STATIC_FP64) * 1000
+    assert out["achieved"] == pytest.approx(flops / 1e-3 / 1e12)
+    assert out["stage_view"]["stage_ms"] == pytest.approx(3.0)

@@ -12,10 +12,10 @@ from paper_2006_07964_gb300 import build, hx
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "hx.h")).read()
+def _declared(header="hx.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(hx_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(hx_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -51,3 +51,13 @@ def test_no_gpu_means_error_not_fallback(lib):
 
 def test_library_is_built_for_sm_103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_probe_library_exports_its_header():
+    """libhx_probe.so (the benchmark's FMA peak probe) exports what
+    include/hx_probe.h declares."""
+    build.build()
+    assert sorted(hx.PROBE_EXPORTS) == _declared("hx_probe.h")
+    lib = ctypes.CDLL(hx.PROBE_PATH)
+    for name in _declared("hx_probe.h"):
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
