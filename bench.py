@@ -91,6 +91,8 @@ WORKLOADS = {
     "batch64": ("64 isentropic-vortex instances, edges from {24..96}, seeded", lambda W: W.batch(64)),
     "shock512": ("two Sod shock tubes in a warped periodic 512x64x64 box, Euler",
                  lambda W: W.shocktube((512, 64, 64), amp=0.02)),
+    "shockvortex512": ("Mach 1.2 shock into an isentropic vortex, warped periodic 512x256x16 box, Euler",
+                       lambda W: W.shock_vortex((512, 256, 16), amp=0.02)),
 }
 
 
@@ -417,7 +419,7 @@ def scheme_report(torch, hx, w, steps, warmup, stream):
     return out
 
 
-ORACLE_REPORT_WORKLOADS = ["vortex32", "tgv128", "shock512", "ogrid", "batch64"]
+ORACLE_REPORT_WORKLOADS = ["vortex32", "tgv128", "shock512", "shockvortex512", "ogrid", "batch64"]
 
 
 def oracle_report(W, steps=2):

@@ -264,18 +264,20 @@ def reindex_block(blocks, b, perm):
 # initial states
 # ---------------------------------------------------------------------------
 
-def isentropic_vortex(gamma, x, y, t=0.0, strength=5.0, u_inf=0.5, L=10.0, centre=(5.0, 5.0)):
+def isentropic_vortex(gamma, x, y, t=0.0, strength=5.0, u_inf=0.5, L=10.0, centre=(5.0, 5.0), Ly=None):
     """Shu's isentropic vortex (strength 5 in Shu's units rho_inf = p_inf = 1),
     mapped to the paper's units by u' = u/sqrt(gamma), p' = p/gamma,
     rho' = rho, t' = sqrt(gamma) t; advected along x at u_inf (paper units,
     u_inf = Mach number since c_inf = 1).  The exact solution at time t is the
     initial vortex moved by u_inf t, taken on the periodic image nearest to
-    each node.  Returns (rho, u, v, w, p)."""
+    each node (periods L along x and Ly, default L, along y).  Returns
+    (rho, u, v, w, p)."""
+    Ly = L if Ly is None else Ly
     xc = centre[0] + u_inf * t
     dx = x - xc
     dx = dx - L * np.round(dx / L)
     dy = y - centre[1]
-    dy = dy - L * np.round(dy / L)
+    dy = dy - Ly * np.round(dy / Ly)
     r2 = dx * dx + dy * dy
     e = np.exp(0.5 * (1.0 - r2))
     du = -strength / (2 * np.pi) * e * dy
@@ -448,3 +450,35 @@ def shocktube(n=(256, 8, 8), length=2.0, amp=0.0, steps=20, left=(1.0, 0.0, 1.0)
     q = conservative(g, rho, u, 0.0, 0.0, p)
     return Workload("shocktube%d" % ni, [Block(xyz, periodic_faces(L), q)], gamma=g, mach=0.0, viscous=False,
                     cfl=0.5, steps=steps, meta={"L": L, "left": left, "right": right})
+
+
+def shock_vortex(n=(128, 64, 8), length=10.0, amp=0.04, mach_s=1.2, strength=3.0, steps=40):
+    """Shock-vortex interaction in a periodic box [0, length) x [0, length
+    n_j/n_i) x [0, length n_k/n_i), Euler.  Gas at rest (rho = 1, p =
+    1/gamma, c = 1) holds an isentropic vortex (Shu's, at rest, strength
+    `strength`) centred at x = 0.55 length, y = half the box; a normal shock
+    of Mach mach_s moving along +x stands at x = 0.45 length, with the
+    Rankine-Hugoniot post-shock state behind it back to x = 0.1 length, so
+    that the shock runs into the vortex from the first step and both the
+    shock and the vortex are bent across y (the nonlinear weights act along
+    every direction of the warped grid).  amp > 0 warps the grid as
+    warped_box does."""
+    ni, nj, nk = n
+    L = (length, length * nj / ni, length * nk / ni)
+    xyz = warped_box(n, L, amp) if amp > 0 else np.stack(lattice(n, L))
+    g = 1.4
+    rho, u, v, w, p = isentropic_vortex(g, xyz[0], xyz[1], strength=strength, u_inf=0.0, L=L[0],
+                                        centre=(0.55 * length, 0.5 * L[1]), Ly=L[1])
+    # Rankine-Hugoniot: shock at speed mach_s into gas at rest (rho 1, p 1/gamma, c 1)
+    m2 = mach_s * mach_s
+    p2 = (1.0 / g) * (1.0 + 2.0 * g / (g + 1.0) * (m2 - 1.0))
+    r2 = (g + 1.0) * m2 / ((g - 1.0) * m2 + 2.0)
+    u2 = mach_s * (1.0 - 1.0 / r2)
+    behind = (xyz[0] >= 0.1 * length) & (xyz[0] < 0.45 * length)
+    rho = np.where(behind, r2, rho)
+    u = np.where(behind, u2, u)
+    v = np.where(behind, 0.0, v)
+    p = np.where(behind, p2, p)
+    q = conservative(g, rho, u, v, w, p)
+    return Workload("shockvortex%d" % ni, [Block(xyz, periodic_faces(L), q)], gamma=g, mach=0.0, viscous=False,
+                    cfl=0.5, steps=steps, meta={"L": L, "mach_s": mach_s, "strength": strength})

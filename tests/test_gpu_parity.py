@@ -144,6 +144,7 @@ CASES = {
     "ogrid_s4": lambda: W.ogrid(scale=4),
     "ogrid_s8": lambda: W.ogrid(scale=8),
     "shock_warped": lambda: W.shocktube((96, 12, 12), amp=0.04),
+    "shock_vortex": lambda: W.shock_vortex((64, 32, 8), amp=0.04),
     "tiny_ns3": lambda: split(warped((24, 8, 8), viscous=True, reynolds=50.0), (3, 1, 1)),
     "min6": lambda: warped((6, 6, 6), viscous=True, reynolds=50.0),
     "rotated_euler": lambda: rotated(warped((28, 24, 20)), (2, 2, 1), {1: (3, 1, 2), 2: (-1, -2, 3), 3: (1, -3, 2)}),
@@ -210,7 +211,7 @@ def test_free_stream_residual_gpu():
 @pytest.mark.parametrize("name,steps", [("vortex32", 10), ("ragged_euler", 4), ("tgv24", 5), ("split_ns", 3),
                                         ("ogrid_s4", 5), ("shock_warped", 20), ("rotated_euler", 4),
                                         ("rotated_ns", 3), ("tiny_ns3", 4), ("min6", 4), ("channel_ns", 5),
-                                        ("duct_euler", 10), ("duct_ns", 5)])
+                                        ("duct_euler", 10), ("duct_ns", 5), ("shock_vortex", 30)])
 def test_steps_parity(name, steps):
     w, ctx, P = pair(name)
     dt, _ = P.dt(0.5)
@@ -708,7 +709,8 @@ def test_residual_norm_matches_oracle(name):
 
 # ---------------------------------------------------------------- original AFWENO (scheme 1)
 
-@pytest.mark.parametrize("name,steps", [("vortex32", 5), ("ragged_ns", 3), ("ogrid_s8", 3), ("shock_warped", 10)])
+@pytest.mark.parametrize("name,steps", [("vortex32", 5), ("ragged_ns", 3), ("ogrid_s8", 3), ("shock_warped", 10),
+                                        ("shock_vortex", 10)])
 def test_original_afweno_parity(name, steps):
     """The original AFWENO of Fig. 9 (characteristic space at the face) on
     the GPU against the oracle's: residual and state after the steps."""
