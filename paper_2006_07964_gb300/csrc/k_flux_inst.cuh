@@ -1,7 +1,10 @@
 // k_flux_inst.cuh -- instantiates the flux kernel for one working precision
 // (HX_FLUX_R) and one direction (HX_FLUX_DIR) in its own translation unit,
 // so the heavy instantiations compile in parallel.
+#include <type_traits>
+
 #include "k_flux.cuh"
+#include "k_flux2.cuh"
 #include "kernels.h"
 
 #define HX_CAT3_(a, b, c) a##b##c
@@ -16,19 +19,35 @@ constexpr int flux_na(int dir, int v) { return dir == 0 ? (v == 0 ? 8 : v == 1 ?
 
 namespace {
 
+// The mixed form's sweeps of the modified scheme (FP32, SCH 0) that store
+// the accumulator run the two-lines-per-thread kernel of k_flux2.cuh
+// (TP x NA/2 threads); everything else, including the sweep with the fused
+// RK stage, runs k_flux.  Measured on the 384^3 Taylor-Green block: xi
+// 2.76 -> 2.51 ms, eta 2.73 -> 2.23 ms, but zeta + RK 4.45 -> 4.66 ms (the
+// packed kernel holds 16 warps per SM, which the latency-bound RK epilogue
+// needs more of).
 template <class R, int DIR, int V, bool VISC, bool RK = false, int SCH = 0>
 struct FluxInst {
     static constexpr int TP = flux_tp(DIR, V), NA = flux_na(DIR, V);
-    static constexpr size_t smem = FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC>();
+    static constexpr bool PAIR = std::is_same<R, float>::value && SCH == 0 && !RK;
+    static constexpr int NT = PAIR ? TP * NA / 2 : TP * NA;
+    static constexpr size_t smem = PAIR ? Flux2Layout<DIR, TP, NA / 2>::smem_bytes(VISC)
+                                        : FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC>();
+    static auto kernel() {
+        if constexpr (PAIR)
+            return k_flux2<DIR, TP, NA / 2, VISC, RK>;
+        else
+            return k_flux<R, DIR, TP, NA, VISC, RK, SCH>;
+    }
     static int ctas() {
-        cudaFuncSetAttribute(k_flux<R, DIR, TP, NA, VISC, RK, SCH>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        auto kern = k_flux<R, DIR, TP, NA, VISC, RK, SCH>;
+        auto kern = kernel();
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TP * NA, smem) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
@@ -37,9 +56,14 @@ struct FluxInst {
     static cudaError_t run(const FluxArgs& a, cudaStream_t s) {
         GasR<R> gs;
         gs.init(a.gas);
-        k_flux<R, DIR, TP, NA, VISC, RK, SCH><<<a.grid, TP * NA, smem, s>>>(
-            a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, (const R*)a.nrm, a.fs,
-            (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
+        if constexpr (PAIR)
+            k_flux2<DIR, TP, NA / 2, VISC, RK><<<a.grid, NT, smem, s>>>(
+                a.blocks, a.tiles, a.ntiles, (const float*)a.Q, (const float*)a.met, a.fs, (const float*)a.stress,
+                (float*)a.A, a.accumulate, gs, a.rk);
+        else
+            k_flux<R, DIR, TP, NA, VISC, RK, SCH><<<a.grid, NT, smem, s>>>(
+                a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, (const R*)a.nrm, a.fs,
+                (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
         return cudaGetLastError();
     }
 };

@@ -414,54 +414,130 @@ k_prim(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
 // the node stress tensor and work + heat-flux vector (9 fields) that every
 // direction's viscous flux projects; otherwise the 12 gradients.
 //
-// Register targets: FP32 fits five CTAs of 256 threads per SM (48
-// registers, with a few spills to L1): this latency-bound kernel gains from
-// the warps (0.104 -> 0.097 ms at 128^3, six CTAs 0.098).  FP64 keeps the
-// compiler's default (0; an explicit 1 lets it take 104 registers).
+// Column tiles: a CTA owns a 32 x 8 (i, j) tile of a block and marches it
+// along k over a segment of `nk` planes (the brick's extent along k).  Each
+// thread keeps the primitives of its own column at k-3..k+3 in registers
+// (the k derivative); each plane k is staged in shared memory with three
+// halo nodes along i and j (the i and j derivatives; corners are never
+// read).  A node's primitives are read about twice from global memory
+// (own column once, halos of the neighbouring tiles) instead of 19 times.
+// Register targets: two CTAs per SM in FP32 (128 registers), one in FP64.
+constexpr int kColX = 32, kColY = 8;
+
 template <class R, bool STRESS>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 0)
-k_grad(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const R* __restrict__ prim,
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1)
+k_grad(const Brick* __restrict__ cols, int nb, const DevBlock* __restrict__ blocks, const R* __restrict__ prim,
        const R* __restrict__ met, long long fs, R* __restrict__ out, GasR<R> gs) {
+    __shared__ R sp[4][kColY + 6][kColX + 6];
+    const int ti = threadIdx.x & 31, tj = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < nb; t += gridDim.x) {
-        const Brick br = bricks[t];
-        int i, j, k;
-        bool ok;
-        brick_node(br, i, j, k, ok);
-        if (!ok) continue;
+        const Brick br = cols[t];
         const DevBlock B = blocks[br.b];
-        const long long e = node_index(B, i, j, k);
-        const int id[3] = {i, j, k};
-        R dc[4][3];
+        const int i = br.i0 + ti, j = br.j0 + tj;
+        const bool own = ti < br.ni && tj < br.nj;
+        bool lo[3], hi[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const long long st = a == 0 ? 1 : (a == 1 ? B.sj : B.sk);
-            const bool lo = (B.phys >> (2 * a)) & 1, hi = (B.phys >> (2 * a + 1)) & 1;
+            lo[a] = (B.phys >> (2 * a)) & 1;
+            hi[a] = (B.phys >> (2 * a + 1)) & 1;
+        }
+        // this thread's halo node of each plane, if any: three nodes beyond
+        // the tile along i (tile rows) or along j (tile columns)
+        const int hxn = 6 * br.nj, hyn = 6 * br.ni;
+        const int h = threadIdx.x;
+        int hx_ = 0, hy_ = 0;
+        const bool halo = h < hxn + hyn;
+        if (h < hxn) {
+            hy_ = h / 6;
+            const int r = h - 6 * hy_;
+            hx_ = r < 3 ? r - 3 : br.ni + r - 3;
+        } else if (halo) {
+            const int u = h - hxn;
+            hx_ = u % br.ni;
+            const int r = u / br.ni;
+            hy_ = r < 3 ? r - 3 : br.nj + r - 3;
+        }
+        const long long hoff = hx_ + (long long)hy_ * B.sj - (long long)ti - (long long)tj * B.sj;
+        // loads of plane k issued one plane ahead (own column at k + 3, the
+        // halo node and the metrics at k), so that they arrive while plane
+        // k - 1 is computed
+        R qv[7][4], nq[4], nh[4], nm[10];
+        auto fetch = [&](int k) {
+            const long long e = node_index(B, i, j, k);
+            if (own) {
+                const long long e3 = hx_chk(B, e + 3 * (long long)B.sk);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const R* f0 = prim + v * fs;
-                auto f = [&](int s) { return f0[hx_chk(B, e + s * st)]; };
-                dc[v][a] = dline<R>(f, id[a], B.n[a], lo, hi);
+                for (int v = 0; v < 4; ++v) nq[v] = prim[v * fs + e3];
+#pragma unroll
+                for (int c = 0; c < 10; ++c) nm[c] = met[c * fs + e];
+            }
+            if (halo) {
+                const long long eh = hx_chk(B, e + hoff);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) nh[v] = prim[v * fs + eh];
+            }
+        };
+        if (own) {   // own column at k0-3 .. k0+2 (slots 1..6; the loop shifts first)
+#pragma unroll
+            for (int s = 1; s < 7; ++s) {
+                const long long e = node_index(B, i, j, br.k0 - 4 + s);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) qv[s][v] = prim[v * fs + e];
             }
         }
-        const R J = met[9 * fs + e];
-        R m[9];
+        fetch(br.k0);
+        for (int kk = 0; kk < br.nk; ++kk) {
+            const int k = br.k0 + kk;
+            R m[10];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) m[c] = met[c * fs + e];
-        R g[12];
+            for (int s = 0; s < 6; ++s)
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
+                for (int v = 0; v < 4; ++v) qv[s][v] = qv[s + 1][v];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                g[v * 3 + c] = J * (m[c] * dc[v][0] + m[3 + c] * dc[v][1] + m[6 + c] * dc[v][2]);
-        if (STRESS) {
-            R S[9];
-            stress(gs, prim[e], prim[fs + e], prim[2 * fs + e], prim[3 * fs + e], g, S);
+            for (int v = 0; v < 4; ++v) qv[6][v] = nq[v];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) out[c * fs + e] = S[c];
-            push_ghosts<R>(blocks, B, br.b, id, out, fs, 9, S, false);   // the stress halo of the sweeps
-        } else {
+            for (int c = 0; c < 10; ++c) m[c] = nm[c];
+            __syncthreads();   // the previous plane's readers are done
+            if (own) {
 #pragma unroll
-            for (int c = 0; c < 12; ++c) out[c * fs + e] = g[c];
+                for (int v = 0; v < 4; ++v) sp[v][tj + 3][ti + 3] = qv[3][v];
+            }
+            if (halo) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) sp[v][hy_ + 3][hx_ + 3] = nh[v];
+            }
+            __syncthreads();
+            if (kk + 1 < br.nk) fetch(k + 1);
+            if (!own) continue;
+            const long long e = node_index(B, i, j, k);
+            R dc[4][3];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                auto fi = [&](int s) { return sp[v][tj + 3][ti + 3 + s]; };
+                auto fj = [&](int s) { return sp[v][tj + 3 + s][ti + 3]; };
+                auto fk = [&](int s) { return qv[3 + s][v]; };
+                dc[v][0] = dline<R>(fi, i, B.n[0], lo[0], hi[0]);
+                dc[v][1] = dline<R>(fj, j, B.n[1], lo[1], hi[1]);
+                dc[v][2] = dline<R>(fk, k, B.n[2], lo[2], hi[2]);
+            }
+            const R J = m[9];
+            R g[12];
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    g[v * 3 + c] = J * (m[c] * dc[v][0] + m[3 + c] * dc[v][1] + m[6 + c] * dc[v][2]);
+            if (STRESS) {
+                R S[9];
+                stress(gs, qv[3][0], qv[3][1], qv[3][2], qv[3][3], g, S);
+#pragma unroll
+                for (int c = 0; c < 9; ++c) out[c * fs + e] = S[c];
+                const int id[3] = {i, j, k};
+                push_ghosts<R>(blocks, B, br.b, id, out, fs, 9, S, false);   // the stress halo of the sweeps
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) out[c * fs + e] = g[c];
+            }
         }
     }
 }

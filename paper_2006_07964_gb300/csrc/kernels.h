@@ -56,7 +56,8 @@ cudaError_t launch_normals(const Brick* bricks, int nb, const DevBlock* blocks, 
 cudaError_t launch_prim(const Brick* bricks, int nb, const DevBlock* blocks, const void* Q, bool fp64,
                         long long fs, void* prim, Gas gas, cudaStream_t s);
 // Gradients (u,v,w,T)_(x,y,z) (12 fields, stress_mode = false) or the node
-// stress tensor and work + heat-flux vector (9 fields, stress_mode = true).
+// stress tensor and work + heat-flux vector (9 fields, stress_mode = true),
+// over column bricks (at most 32 x 8 nodes in (i, j), any extent along k).
 cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, const void* prim, const void* met,
                         bool fp64, long long fs, void* out, bool stress_mode, Gas gas, cudaStream_t s);
 // Checking aid: NaN into the ghost shell of nf fields (bricks cover the padded box).

@@ -75,6 +75,8 @@ struct hx_ctx {
     int ntiles[3][kFluxVariants] = {};
     Brick *d_int = nullptr, *d_prim = nullptr;
     int n_int = 0, n_prim = 0;
+    Brick* d_col = nullptr;     // gradient / stress kernel: 32 x 8 (i, j) tiles over segments along k
+    int n_col = 0;
     Brick* d_shell = nullptr;   // debug_poison: bricks over every block's padded box
     int n_shell = 0;
     NodeItem* d_bc = nullptr;       // far-field boundary nodes
@@ -305,7 +307,7 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
     }
     if (visc) {
         if (pf) pf->begin(K_GRAD);
-        HX_CK(launch_grad(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, true,
+        HX_CK(launch_grad(ctx->d_col, ctx->n_col, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, true,
                           ctx->gas, s));
         if (pf) pf->end();
     }
@@ -420,8 +422,12 @@ int autotune(hx_ctx* ctx) {
             cudaEvent_t e0, e1;
             HX_CK(cudaEventCreate(&e0));
             HX_CK(cudaEventCreate(&e1));
+            // zeta: the steps run the sweep with the fused RK stage, so that is
+            // the one timed (stage-2 coefficients, output into the stage
+            // buffers Q^(2) and its FP32 copy, which hold nothing between steps)
+            const bool rk = d == 2;
             for (int v = 0; v < kFluxVariants; ++v) {
-                const int cps = flux_ctas_per_sm(f64, d, v, visc, false, ctx->cfg.scheme);
+                const int cps = flux_ctas_per_sm(f64, d, v, visc, rk, ctx->cfg.scheme);
                 if (cps <= 0) continue;
                 FluxArgs a{};
                 a.blocks = ctx->d_blocks;
@@ -437,6 +443,21 @@ int autotune(hx_ctx* ctx) {
                 a.gas = ctx->gas;
                 a.scheme = ctx->cfg.scheme;
                 a.grid = (int)std::min<long long>(a.ntiles, (long long)cps * ctx->num_sms);
+                if (rk) {
+                    a.fuse_rk = 1;
+                    a.rk.Qn = ctx->Qn;
+                    a.rk.Qk = ctx->Qn;
+                    a.rk.metd = ctx->met;
+                    a.rk.Qout = ctx->Qb;
+                    a.rk.Qfout = f64 ? nullptr : ctx->Qf[2];
+                    a.rk.Aref = ctx->Aref;
+                    a.rk.ca = 0.75;
+                    a.rk.cb = 0.25;
+                    a.rk.cc = 0.25;
+                    a.rk.ccf = -0.25f;
+                    a.rk.gm1 = ctx->gas.gamma - 1.0;
+                    a.rk.flags = ctx->d_flags;
+                }
                 HX_CK(launch_flux(f64, d, v, visc, a, ctx->stream));   // warm-up
                 HX_CK(cudaEventRecord(e0, ctx->stream));
                 const int reps = 3;
@@ -453,6 +474,7 @@ int autotune(hx_ctx* ctx) {
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
+            HX_CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(unsigned), ctx->stream));
         } else {   // the 128-thread tile (16 x 8 along xi, 8 x 16 across), else the first that launches
             const int order[kFluxVariants] = {2, 0, 1};
             for (int o = 0; o < kFluxVariants && best < 0; ++o)
@@ -873,6 +895,25 @@ int hx_finalize(hx_ctx* ctx) {
             add_bricks(bg, b, l2, h2);
         }
     }
+    {   // column tiles: segments along k short enough that the launch has
+        // about 16 CTAs per SM, at least 8 planes each
+        long long cols = 0;
+        for (auto& H : ctx->blocks) cols += (long long)((H.n[0] + 31) / 32) * ((H.n[1] + 7) / 8);
+        const long long want = 16LL * ctx->num_sms;
+        const int segs = (int)std::max<long long>(1, (want + cols - 1) / cols);
+        std::vector<Brick> bc;
+        for (int b = 0; b < nb; ++b) {
+            const HostBlock& H = ctx->blocks[b];
+            const int kc = std::max(8, (H.n[2] + segs - 1) / segs);
+            for (int k = 0; k < H.n[2]; k += kc)
+                for (int j = 0; j < H.n[1]; j += 8)
+                    for (int i = 0; i < H.n[0]; i += 32)
+                        bc.push_back(Brick{b, i, j, k, std::min(32, H.n[0] - i), std::min(8, H.n[1] - j),
+                                           std::min(kc, H.n[2] - k), 0});
+        }
+        ctx->n_col = (int)bc.size();
+        if ((rc = upload(ctx, &ctx->d_col, bc))) return rc;
+    }
     bp = bi;
     bp.insert(bp.end(), bg.begin(), bg.end());
     ctx->n_int = (int)bi.size();
@@ -1033,7 +1074,7 @@ int hx_get_gradients(hx_ctx* ctx, int block, double* g_out, int on_device) {
     void* Qs = stencil_state(ctx, 0);
     const void* M = stencil_met(ctx);
     HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, ctx->gas, ctx->stream));
-    HX_CK(launch_grad(ctx->d_int, ctx->n_int, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, false, ctx->gas,
+    HX_CK(launch_grad(ctx->d_col, ctx->n_col, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, false, ctx->gas,
                       ctx->stream));
     return get_field(ctx, block, ctx->grad, f64, 12, g_out, on_device);
 }
