@@ -89,6 +89,49 @@ __device__ __forceinline__ bool nonfinite_bits(double x) {
     return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
 }
 
+// Exact FP32 -> FP64 widening and FP64 -> FP32 narrowing (IEEE 754
+// round-to-nearest-even) on the integer pipe.  GB300 executes the
+// conversion instructions on its FP64 unit, whose rate is 1/64 of FP32;
+// a point-parallel kernel with ten FP64 FMAs per node is held by it.  Both
+// follow the binary formats bit by bit (sign, exponent rebias by 896,
+// mantissa shift by 29), subnormals and non-finite values included.
+__device__ __forceinline__ double widen_f32(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned s = b & 0x80000000u, em = b & 0x7fffffffu;
+    if (em >= 0x00800000u && em < 0x7f800000u)   // normal
+        return __hiloint2double((int)(s | ((em >> 3) + (896u << 20))), (int)(em << 29));
+    if (em == 0u) return __hiloint2double((int)s, 0);
+    if (em >= 0x7f800000u)   // infinity, or a quiet NaN
+        return __hiloint2double((int)(s | (em == 0x7f800000u ? 0x7ff00000u : 0x7ff80000u)), 0);
+    // subnormal em * 2^-149: the leading bit n becomes the implicit one
+    const int n = 31 - __clz(em);
+    const unsigned long long m = ((unsigned long long)em << (52 - n)) & 0x000fffffffffffffULL;
+    return __longlong_as_double((long long)(((unsigned long long)s << 32) |
+                                            ((unsigned long long)(n + 874) << 52) | m));
+}
+
+__device__ __forceinline__ float narrow_f64_rn(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned s = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e == 0x7ff) return __uint_as_float(s | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
+    const int fe = e - 896;   // biased FP32 exponent
+    if (fe >= 0xff) return __uint_as_float(s | 0x7f800000u);
+    if (fe > 0) {   // normal: keep 23 mantissa bits, round the other 29 to nearest, ties to even
+        const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu;
+        const unsigned r = (((unsigned)fe << 23) | mant) + ((rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) ? 1u : 0u);
+        return __uint_as_float(s | r);   // a carry moves into the exponent (up to infinity)
+    }
+    if (e == 0) return __uint_as_float(s);   // zero, or an FP64 subnormal
+    // FP32 subnormal (or zero) result: the 53-bit significand times 2^(e - 926)
+    const unsigned long long m = ((((unsigned long long)(hi & 0xfffffu)) << 32) | lo) | (1ULL << 52);
+    const int sh = 926 - e;   // >= 30
+    if (sh >= 64) return __uint_as_float(s);
+    const unsigned long long q = m >> sh, rem = m & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1);
+    return __uint_as_float(s | (unsigned)(q + ((rem > half || (rem == half && (q & 1ULL))) ? 1ULL : 0ULL)));
+}
+
 // HaloItem.mode: bits 0-3 kind, bits 4-5 direction, bit 6 side (1 = + face),
 // bits 8.. translation index (coordinates).
 enum : int { HM_COPY = 0, HM_WALL = 1, HM_FARFIELD = 2, HM_TRANSLATE = 3, HM_REFLECT = 4 };

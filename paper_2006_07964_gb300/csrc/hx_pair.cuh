@@ -193,15 +193,4 @@ __device__ __forceinline__ P2 dline_p(const F& f, int p, int n, bool lo, bool hi
     return d6p(f(-3), f(-2), f(-1), f(1), f(2), f(3));
 }
 
-// Primitives (u, v, w, T) of a packed conservative state: the scalar
-// primitives of hx_common.cuh, packed.
-__device__ __forceinline__ void primitives_p(const GasR<float>& gs, const P2 q[5], P2 pv[4]) {
-    const P2 irho = prcp(q[0]);
-    pv[0] = q[1] * irho;
-    pv[1] = q[2] * irho;
-    pv[2] = q[3] * irho;
-    const P2 p = pk(gs.gm1) * (q[4] - pk(0.5f) * pfma(q[1], pv[0], pfma(q[2], pv[1], q[3] * pv[2])));
-    pv[3] = pk(gs.gamma) * p * irho;
-}
-
 }  // namespace hx

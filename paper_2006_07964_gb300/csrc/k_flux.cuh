@@ -73,11 +73,10 @@ struct FluxLayout {
     }
 };
 
-// RK (last sweep only): instead of storing A, finish R = -J (A + div) and
-// the RK3 stage combination at each output node (Eq. (20), FP64), with the
-// wall-node values and the non-finite / non-physical flags; the mixed form
-// also writes the FP32 copy of the stage output and, when asked
-// (rk.primout), its primitives for the next stage.
+// RK (last sweep of the FP64 form only): instead of storing A, finish
+// R = -J (A + div) and the RK3 stage combination at each output node
+// (Eq. (20)), with the wall-node values and the non-finite / non-physical
+// flags.  The mixed form ends its stages in k_rk_stage instead.
 // SCH 0: modified AFWENO (characteristic space at the node, Figs. 10-11);
 // SCH 1: original AFWENO (characteristic space at the face from the mean
 // state and the face metric, two independent WENOs per face, Fig. 9).
@@ -156,11 +155,10 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
             }
             // ---- L2 prefetches (FP32 sweeps; each thread owns one node of
             // every step): what this chunk's output step reads from global
-            // memory (the accumulator, the fused RK stage's inputs), and what
-            // the next chunk's load and node steps read (state, metric,
-            // stress).  Issued now, they arrive while the stencil phases run
-            // (measured on the 128^3 Taylor-Green sweeps: eta 0.124 -> 0.116
-            // ms, zeta + RK 0.214 -> 0.198 ms).
+            // memory (the accumulator), and what the next chunk's load and
+            // node steps read (state, metric, stress).  Issued now, they arrive
+            // while the stencil phases run (measured on the 128^3 Taylor-Green
+            // sweeps: eta 0.124 -> 0.116 ms).
             if (sizeof(R) == 4) {
                 // Opaque copies of the thread index and the field stride, so
                 // that none of this address arithmetic is shared with the
@@ -173,28 +171,13 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                 LY::split(tq, TP, p, a);
                 const bool line = a0 + a < na;
                 const int po = base - 2 + p;   // this chunk's output node
-                if ((accumulate || RK) && line && po >= 0 && po < n) {
+                if (accumulate && line && po >= 0 && po < n) {
                     const long long e = hx_chk(B, e0 + po * sd + a * sa);
-                    if (accumulate) {
 #pragma unroll
-                        for (int k = 0; k < 5; ++k) prefetch_l2(A + k * fq + e);
-                    }
-                    if (RK) {
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            prefetch_l2(rk.Qn + k * fq + e);
-                            if (rk.cb != 0.0) prefetch_l2(rk.Qk + k * fq + e);
-                            if (rk.Aref) prefetch_l2(rk.Aref + k * fq + e);
-                        }
-                        prefetch_l2(met + 9 * fq + e);
-                        if (rk.dtl) prefetch_l2(rk.dtl + e);
-                    }
+                    for (int k = 0; k < 5; ++k) prefetch_l2(A + k * fq + e);
                 }
-                // The next chunk's inputs: not in the fused RK sweep, which
-                // already prefetches its stage inputs (with them as well it
-                // measured 10 % slower).
                 const int pl = base + TP + 3 + p;   // the next chunk's load node
-                if (!RK && line && pl <= n + 2) {
+                if (line && pl <= n + 2) {
                     const long long e = hx_chk(B, e0 + pl * sd + a * sa);
 #pragma unroll
                     for (int f = 0; f < 5; ++f) prefetch_l2(Q + f * fq + e);
@@ -202,7 +185,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     for (int f = 0; f < 3; ++f) prefetch_l2(met + (3 * DIR + f) * fq + e);
                 }
                 const int pn = base + TP + 1 + p;   // the next chunk's node step
-                if (!RK && VISC && line && pn <= n + 2 && !(hi && pn >= n)) {
+                if (VISC && line && pn <= n + 2 && !(hi && pn >= n)) {
                     const long long e = hx_chk(B, e0 + pn * sd + a * sa);
 #pragma unroll
                     for (int f = 0; f < 9; ++f) prefetch_l2(stress + f * fq + e);
@@ -378,32 +361,14 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
 #pragma unroll
                     for (int k = 0; k < 5; ++k) A[k * fs + e] = dv[k];
                 } else {
-                    if (rk.Aref) {
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) dv[k] -= (R)rk.Aref[k * fs + e];
-                    }
+                    static_assert(!RK || sizeof(R) == 8, "the fused RK stage is the FP64 form's");
                     double qo[5];
-                    if constexpr (sizeof(R) == 4) {
-                        // Mixed form: the increment -cc dt J A is formed in FP32,
-                        // the precision A has; its combination with Q^n and Q^(k)
-                        // is FP64, one or two FMAs per field.  (GB300 runs the
-                        // format conversions on its FP64 unit; bit-operation
-                        // conversions on the integer pipe measured slower here,
-                        // as they lengthen this latency-bound epilogue.)
-                        const float f = rk.ccf * (float)(rk.dtl ? rk.dtl[e] : B.dt) * met[9 * fs + e];
+                    const double f = -rk.cc * (rk.dtl ? rk.dtl[e] : B.dt) * rk.metd[9 * fs + e];
 #pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            const double r = (double)(f * dv[k]);
-                            qo[k] = fma(rk.ca, rk.Qn[k * fs + e], rk.cb != 0.0 ? fma(rk.cb, rk.Qk[k * fs + e], r) : r);
-                        }
-                    } else {
-                        const double f = -rk.cc * (rk.dtl ? rk.dtl[e] : B.dt) * rk.metd[9 * fs + e];
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            double v = rk.ca * rk.Qn[k * fs + e] + f * (double)dv[k];
-                            if (rk.cb != 0.0) v += rk.cb * rk.Qk[k * fs + e];
-                            qo[k] = v;
-                        }
+                    for (int k = 0; k < 5; ++k) {
+                        double v = rk.ca * rk.Qn[k * fs + e] + f * (double)dv[k];
+                        if (rk.cb != 0.0) v += rk.cb * rk.Qk[k * fs + e];
+                        qo[k] = v;
                     }
                     if (B.wall) {   // node indices of this output (line groups start at sweep index 0)
                         const int ni_ = DIR == 0 ? p : T.i0 + a;
@@ -424,28 +389,9 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         bad = bad || nonfinite_bits(qo[k]);
                         rk.Qout[k * fs + e] = qo[k];
                     }
-                    if (rk.Qfout) {
-                        float qv[5];
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            qv[k] = (float)qo[k];
-                            rk.Qfout[k * fs + e] = qv[k];
-                        }
-                        if constexpr (sizeof(R) == 4) {
-                            if (rk.primout) {   // the next stage's primitives, from the FP32 copy as in k_prep
-                                float pv[4];
-                                primitives(gs, qv, pv);
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) rk.primout[k * fs + e] = pv[k];
-                            }
-                        }
-                        if (!bad && !(qv[0] > 0.0f &&
-                                      qv[4] * qv[0] - 0.5f * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) > 0.0f))
-                            atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
-                    } else if (!bad && !(qo[0] > 0.0 &&
-                                         qo[4] * qo[0] - 0.5 * (qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) > 0.0)) {
+                    if (!bad &&
+                        !(qo[0] > 0.0 && qo[4] * qo[0] - 0.5 * (qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) > 0.0))
                         atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
-                    }
                     if (bad) atomicOr(rk.flags, (unsigned)FLAG_NONFINITE);
                 }
             }

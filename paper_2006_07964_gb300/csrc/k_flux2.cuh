@@ -3,9 +3,9 @@
 //
 // It computes what k_flux<float, ...> computes (the modified AFWENO of
 // Sec. 4.5.1, Figs. 10-11, Steger-Warming face fluxes, Eq. (19), the
-// viscous node flux of Eqs. (5)-(6) and its central derivative, and in the
-// last sweep R = -J A with the FP64 RK3 stage of Eq. (20)), with the same
-// ring of chunks in shared memory, but every thread owns a pair of adjacent
+// viscous node flux of Eqs. (5)-(6) and its central derivative, accumulated
+// into A; the stage's RK update follows in k_rk_stage), with the same ring
+// of chunks in shared memory, but every thread owns a pair of adjacent
 // lines and works on both with the packed FP32 instructions of hx_pair.cuh:
 // the arithmetic, the shared-memory accesses (64-bit) and the index
 // arithmetic are issued once for two nodes.  GB300 executes the scalar
@@ -69,11 +69,11 @@ constexpr int flux2_min_ctas() {
     return 2048 / 4 / NT;
 }
 
-template <int DIR, int TP, int NP, bool VISC, bool RK>
+template <int DIR, int TP, int NP, bool VISC>
 __global__ void __launch_bounds__(TP * NP, flux2_min_ctas<TP * NP>())
 k_flux2(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int ntiles, const float* __restrict__ Q,
         const float* __restrict__ met, long long fs, const float* __restrict__ stress, float* __restrict__ A,
-        int accumulate, GasR<float> gs, RKArgs rk) {
+        int accumulate, GasR<float> gs) {
     using LY = Flux2Layout<DIR, TP, NP>;
     constexpr int PL = LY::PL;
     constexpr int NT = TP * NP;
@@ -115,9 +115,8 @@ k_flux2(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int
                     for (int f = 0; f < 3; ++f) st2(sM + f * PL + s, gld2<DIR>(met + (3 * DIR + f) * fs, e, sa));
                 }
             }
-            // ---- L2 prefetches: this chunk's output-step inputs (accumulator,
-            // the fused RK stage's FP64 inputs) and, outside the fused sweep,
-            // the next chunk's state, metric and stress (as k_flux<float>)
+            // ---- L2 prefetches: this chunk's accumulator and the next chunk's
+            // state, metric and stress (as k_flux<float>)
             {
                 int tq = tid;
                 long long fq = fs;
@@ -126,29 +125,16 @@ k_flux2(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int
                 LY::split(tq, TP, p, a2);
                 const bool line = a0 + 2 * a2 < na;
                 const int po = base - 2 + p;
-                if ((accumulate || RK) && line && po >= 0 && po < n) {
+                if (accumulate && line && po >= 0 && po < n) {
                     const long long e = hx_chk(B, e0 + po * sd + 2 * a2 * sa);
 #pragma unroll
                     for (int l = 0; l < (DIR == 0 ? 2 : 1); ++l) {
-                        const long long el = e + l * sa;
-                        if (accumulate) {
 #pragma unroll
-                            for (int k = 0; k < 5; ++k) prefetch_l2(A + k * fq + el);
-                        }
-                        if (RK) {
-#pragma unroll
-                            for (int k = 0; k < 5; ++k) {
-                                prefetch_l2(rk.Qn + k * fq + el);
-                                if (rk.cb != 0.0) prefetch_l2(rk.Qk + k * fq + el);
-                                if (rk.Aref) prefetch_l2(rk.Aref + k * fq + el);
-                            }
-                            prefetch_l2(met + 9 * fq + el);
-                            if (rk.dtl) prefetch_l2(rk.dtl + el);
-                        }
+                        for (int k = 0; k < 5; ++k) prefetch_l2(A + k * fq + e + l * sa);
                     }
                 }
                 const int pl = base + TP + 3 + p;
-                if (!RK && line && pl <= n + 2) {
+                if (line && pl <= n + 2) {
                     const long long e = hx_chk(B, e0 + pl * sd + 2 * a2 * sa);
 #pragma unroll
                     for (int l = 0; l < (DIR == 0 ? 2 : 1); ++l) {
@@ -159,7 +145,7 @@ k_flux2(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int
                     }
                 }
                 const int pn = base + TP + 1 + p;
-                if (!RK && VISC && line && pn <= n + 2 && !(hi && pn >= n)) {
+                if (VISC && line && pn <= n + 2 && !(hi && pn >= n)) {
                     const long long e = hx_chk(B, e0 + pn * sd + 2 * a2 * sa);
 #pragma unroll
                     for (int l = 0; l < (DIR == 0 ? 2 : 1); ++l) {
@@ -292,73 +278,16 @@ k_flux2(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int
                     }
                     dv[k] = accumulate ? acc[k] + div : div;
                 }
-                if (!RK) {
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        if (DIR == 0) {
-                            A[k * fs + e] = dv[k].v.x;
-                            if (two) A[k * fs + e + sa] = dv[k].v.y;
-                        } else if (two) {
-                            st2(A + k * fs + e, dv[k]);
-                        } else {
-                            A[k * fs + e] = dv[k].v.x;
-                        }
+                for (int k = 0; k < 5; ++k) {
+                    if (DIR == 0) {
+                        A[k * fs + e] = dv[k].v.x;
+                        if (two) A[k * fs + e + sa] = dv[k].v.y;
+                    } else if (two) {
+                        st2(A + k * fs + e, dv[k]);
+                    } else {
+                        A[k * fs + e] = dv[k].v.x;
                     }
-                    continue;
-                }
-                // ---- fused RK stage, lane by lane (FP64)
-                if (rk.Aref) {
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) dv[k] = dv[k] - gld2<DIR>(rk.Aref + k * fs, e, sa);
-                }
-                const P2 Jp = gld2<DIR>(met + 9 * fs, e, sa);
-#pragma unroll
-                for (int l = 0; l < 2; ++l) {
-                    if (l == 1 && !two) break;
-                    const long long el = e + l * sa;
-                    const float J = l ? Jp.v.y : Jp.v.x;
-                    // the increment -cc dt J A in FP32, combined with Q^n and Q^(k) in FP64
-                    const float fr = rk.ccf * (float)(rk.dtl ? rk.dtl[el] : B.dt) * J;
-                    double qo[5];
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        const double r = (double)(fr * (l ? dv[k].v.y : dv[k].v.x));
-                        qo[k] = fma(rk.ca, rk.Qn[k * fs + el], rk.cb != 0.0 ? fma(rk.cb, rk.Qk[k * fs + el], r) : r);
-                    }
-                    if (B.wall) {
-                        const int a = 2 * a2 + l;
-                        const int ni_ = DIR == 0 ? p : T.i0 + a;
-                        const int nj_ = DIR == 1 ? p : (DIR == 0 ? T.j0 + a : T.j0);
-                        const int nk_ = DIR == 2 ? p : T.k0;
-                        const bool on = ((B.wall & 1) && ni_ == 0) || ((B.wall & 2) && ni_ == B.n[0] - 1) ||
-                                        ((B.wall & 4) && nj_ == 0) || ((B.wall & 8) && nj_ == B.n[1] - 1) ||
-                                        ((B.wall & 16) && nk_ == 0) || ((B.wall & 32) && nk_ == B.n[2] - 1);
-                        if (on) {
-                            const double pw =
-                                rk.gm1 * (qo[4] - 0.5 * (qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) / qo[0]);
-                            qo[1] = qo[2] = qo[3] = 0.0;
-                            qo[4] = pw / rk.gm1;
-                        }
-                    }
-                    bool bad = false;
-                    float qv[5];
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        bad = bad || nonfinite_bits(qo[k]);
-                        rk.Qout[k * fs + el] = qo[k];
-                        qv[k] = (float)qo[k];
-                        if (rk.Qfout) rk.Qfout[k * fs + el] = qv[k];
-                    }
-                    if (rk.primout) {   // the next stage's primitives, from the FP32 copy as in k_prep
-                        float pv[4];
-                        primitives(gs, qv, pv);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) rk.primout[k * fs + el] = pv[k];
-                    }
-                    if (!bad && !(qv[0] > 0.0f &&
-                                  qv[4] * qv[0] - 0.5f * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) > 0.0f))
-                        atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
-                    if (bad) atomicOr(rk.flags, (unsigned)FLAG_NONFINITE);
                 }
             }
             // no barrier here: the next chunk's loads touch only state and

@@ -19,23 +19,21 @@ constexpr int flux_na(int dir, int v) { return dir == 0 ? (v == 0 ? 8 : v == 1 ?
 
 namespace {
 
-// The mixed form's sweeps of the modified scheme (FP32, SCH 0) that store
-// the accumulator run the two-lines-per-thread kernel of k_flux2.cuh
-// (TP x NA/2 threads); everything else, including the sweep with the fused
-// RK stage, runs k_flux.  Measured on the 384^3 Taylor-Green block: xi
-// 2.76 -> 2.51 ms, eta 2.73 -> 2.23 ms, but zeta + RK 4.45 -> 4.66 ms (the
-// packed kernel holds 16 warps per SM, which the latency-bound RK epilogue
-// needs more of).
+// The mixed form's sweeps of the modified scheme (FP32, SCH 0) run the
+// two-lines-per-thread kernel of k_flux2.cuh (TP x NA/2 threads); the FP64
+// form and the original scheme run k_flux.  Only the FP64 form fuses the RK
+// stage into its zeta sweep.
 template <class R, int DIR, int V, bool VISC, bool RK = false, int SCH = 0>
 struct FluxInst {
     static constexpr int TP = flux_tp(DIR, V), NA = flux_na(DIR, V);
-    static constexpr bool PAIR = std::is_same<R, float>::value && SCH == 0 && !RK;
+    static constexpr bool PAIR = std::is_same<R, float>::value && SCH == 0;
+    static_assert(!RK || std::is_same<R, double>::value, "the fused RK stage is the FP64 form's");
     static constexpr int NT = PAIR ? TP * NA / 2 : TP * NA;
     static constexpr size_t smem = PAIR ? Flux2Layout<DIR, TP, NA / 2>::smem_bytes(VISC)
                                         : FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC>();
     static auto kernel() {
         if constexpr (PAIR)
-            return k_flux2<DIR, TP, NA / 2, VISC, RK>;
+            return k_flux2<DIR, TP, NA / 2, VISC>;
         else
             return k_flux<R, DIR, TP, NA, VISC, RK, SCH>;
     }
@@ -57,9 +55,9 @@ struct FluxInst {
         GasR<R> gs;
         gs.init(a.gas);
         if constexpr (PAIR)
-            k_flux2<DIR, TP, NA / 2, VISC, RK><<<a.grid, NT, smem, s>>>(
+            k_flux2<DIR, TP, NA / 2, VISC><<<a.grid, NT, smem, s>>>(
                 a.blocks, a.tiles, a.ntiles, (const float*)a.Q, (const float*)a.met, a.fs, (const float*)a.stress,
-                (float*)a.A, a.accumulate, gs, a.rk);
+                (float*)a.A, a.accumulate, gs);
         else
             k_flux<R, DIR, TP, NA, VISC, RK, SCH><<<a.grid, NT, smem, s>>>(
                 a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, (const R*)a.nrm, a.fs,
@@ -76,7 +74,7 @@ template <int SCH, class F>
 auto pick(int v, bool visc, bool rk, F&& f) {
     using R = HX_FLUX_R;
     constexpr int D = HX_FLUX_DIR;
-    constexpr bool CanRK = D == 2;
+    constexpr bool CanRK = D == 2 && std::is_same<R, double>::value;   // the mixed form ends its stages in k_rk_stage
     const int key = v * 4 + (visc ? 2 : 0) + (rk && CanRK ? 1 : 0);
     switch (key) {
         case 0: return f(FluxInst<R, D, 0, false, false, SCH>{});

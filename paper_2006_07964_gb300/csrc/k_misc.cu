@@ -542,6 +542,69 @@ k_grad(const Brick* __restrict__ cols, int nb, const DevBlock* __restrict__ bloc
     }
 }
 
+// The RK3 stage of the mixed form (Eq. (20)) as a streaming pass after the
+// three sweeps: R = -J (A - A_ref) in FP32, the increment -cc dt J A in FP32
+// (the precision A has) and its combination with Q^n and Q^(k) in FP64, the
+// wall-node values, the FP32 copy of the output (rounded to nearest) and,
+// for a stage whose output feeds the next, its FP32 primitives; the
+// non-finite / non-physical flags.  The same arithmetic as the FP32 sweep's
+// fused epilogue (k_flux with RK), which the FP64 form keeps: separated, the
+// stage's FP64 work and its memory traffic overlap in a point-parallel
+// kernel instead of trailing the stencil phases of the zeta sweep, and the
+// format conversions run on the integer pipe (widen_f32, narrow_f64_rn), so
+// that the FP64 unit does only the ten FMAs of the combination.
+__global__ void __launch_bounds__(kThreads, 4)
+k_rk_stage(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const float* __restrict__ A,
+           const float* __restrict__ metf, long long fs, GasR<float> gs, RKArgs rk) {
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const Brick br = bricks[t];
+        int i, j, k;
+        bool ok;
+        brick_node(br, i, j, k, ok);
+        if (!ok) continue;
+        const DevBlock& B = blocks[br.b];
+        const long long e = node_index(B, i, j, k);
+        float dv[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) dv[c] = rk.Aref ? A[c * fs + e] - rk.Aref[c * fs + e] : A[c * fs + e];
+        const float fr = rk.ccf * narrow_f64_rn(rk.dtl ? rk.dtl[e] : B.dt) * metf[9 * fs + e];
+        double qo[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const double r = widen_f32(fr * dv[c]);
+            qo[c] = fma(rk.ca, rk.Qn[c * fs + e], rk.cb != 0.0 ? fma(rk.cb, rk.Qk[c * fs + e], r) : r);
+        }
+        if (B.wall) {
+            const bool on = ((B.wall & 1) && i == 0) || ((B.wall & 2) && i == B.n[0] - 1) ||
+                            ((B.wall & 4) && j == 0) || ((B.wall & 8) && j == B.n[1] - 1) ||
+                            ((B.wall & 16) && k == 0) || ((B.wall & 32) && k == B.n[2] - 1);
+            if (on) {
+                const double pw = rk.gm1 * (qo[4] - 0.5 * (qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) / qo[0]);
+                qo[1] = qo[2] = qo[3] = 0.0;
+                qo[4] = pw / rk.gm1;
+            }
+        }
+        bool bad = false;
+        float qv[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            bad = bad || nonfinite_bits(qo[c]);
+            rk.Qout[c * fs + e] = qo[c];
+            qv[c] = narrow_f64_rn(qo[c]);
+            rk.Qfout[c * fs + e] = qv[c];
+        }
+        if (rk.primout) {   // the next stage's primitives, from the FP32 copy as in k_prep
+            float pv[4];
+            primitives(gs, qv, pv);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) rk.primout[c * fs + e] = pv[c];
+        }
+        if (!bad && !(qv[0] > 0.0f && qv[4] * qv[0] - 0.5f * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) > 0.0f))
+            atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
+        if (bad) atomicOr(rk.flags, (unsigned)FLAG_NONFINITE);
+    }
+}
+
 // Residual R = -J A of one block, packed [5][nk][nj][ni].
 template <class R>
 __global__ void k_rhs_out(DevBlock B, const R* __restrict__ A, const float* __restrict__ Aref,
@@ -834,6 +897,15 @@ cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, con
             k_grad<float, false><<<g, kThreads, 0, s>>>(bricks, nb, blocks, (const float*)prim, (const float*)met,
                                                          fs, (float*)out, gs);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk_stage(const Brick* bricks, int nb, const DevBlock* blocks, const float* A, const float* metf,
+                            long long fs, Gas gas, const RKArgs& rk, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    GasR<float> gs;
+    gs.init(gas);
+    k_rk_stage<<<grid_for((long long)nb * kThreads), kThreads, 0, s>>>(bricks, nb, blocks, A, metf, fs, gs, rk);
     return cudaGetLastError();
 }
 

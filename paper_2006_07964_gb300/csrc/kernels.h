@@ -63,6 +63,10 @@ cudaError_t launch_grad(const Brick* bricks, int nb, const DevBlock* blocks, con
 // Checking aid: NaN into the ghost shell of nf fields (bricks cover the padded box).
 cudaError_t launch_poison(const Brick* bricks, int nb, const DevBlock* blocks, void* p, bool fp64, long long fs,
                           int nf, cudaStream_t s);
+// Mixed form: the RK3 stage (Eq. (20)) of the interior bricks from the
+// accumulated FP32 divergence A (rk.Qfout must be set).
+cudaError_t launch_rk_stage(const Brick* bricks, int nb, const DevBlock* blocks, const float* A, const float* metf,
+                            long long fs, Gas gas, const RKArgs& rk, cudaStream_t s);
 // Far-field boundary nodes after a stage.
 cudaError_t launch_bc_farfield(const NodeItem* items, int n, const DevBlock* blocks, double* Q, float* Qf,
                                float* primf, const double* met, long long fs, Gas gas, cudaStream_t s);

@@ -39,9 +39,9 @@ struct HostBlock {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
-enum Kind { K_PREP, K_GRAD, K_FLUX0, K_FLUX1, K_FLUX2, K_FLUX2RK, K_BC, K_COUNT };
+enum Kind { K_PREP, K_GRAD, K_FLUX0, K_FLUX1, K_FLUX2, K_FLUX2RK, K_BC, K_RK, K_COUNT };
 const char* kKindName[K_COUNT] = {"prep", "stress", "flux_xi", "flux_eta", "flux_zeta", "flux_zeta_rk",
-                                  "bc_farfield"};
+                                  "bc_farfield", "rk_stage"};
 
 // Process-wide autotune cache: (precision, dir, viscous, shape class) -> variant.
 std::mutex g_tune_mu;
@@ -89,7 +89,8 @@ struct hx_ctx {
 
     int variant[3] = {0, 0, 0};
     int grid[3] = {1, 1, 1};
-    int grid_rk = 1;   // zeta sweep with the fused RK stage
+    int grid_rk = 1;   // zeta sweep with the fused RK stage (FP64 form)
+    int grid_z = 1;    // zeta sweep of a mixed-form stage (tuned as such)
     double tune_ms[3][kFluxVariants] = {{-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
     bool tuned = false;
 
@@ -327,7 +328,10 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
         a.gas = ctx->gas;
         a.grid = ctx->grid[d];
         a.scheme = ctx->cfg.scheme;
-        const bool fuse = d == 2 && rk;
+        // FP64: the zeta sweep finishes the stage; mixed: a streaming
+        // kernel does, after the three sweeps (k_rk_stage)
+        const bool fuse = d == 2 && rk && f64;
+        if (d == 2 && rk && !f64) a.grid = ctx->grid_z;
         if (fuse) {
             a.fuse_rk = 1;
             a.rk = *rk;
@@ -335,6 +339,12 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
         }
         if (pf) pf->begin(fuse ? K_FLUX2RK : K_FLUX0 + d);
         HX_CK(launch_flux(f64, d, v, visc, a, s));
+        if (pf) pf->end();
+    }
+    if (rk && !f64) {
+        if (pf) pf->begin(K_RK);
+        HX_CK(launch_rk_stage(ctx->d_int, ctx->n_int, ctx->d_blocks, (const float*)ctx->A, (const float*)M, ctx->fs,
+                              ctx->gas, *rk, s));
         if (pf) pf->end();
     }
     return HX_OK;
@@ -422,10 +432,11 @@ int autotune(hx_ctx* ctx) {
             cudaEvent_t e0, e1;
             HX_CK(cudaEventCreate(&e0));
             HX_CK(cudaEventCreate(&e1));
-            // zeta: the steps run the sweep with the fused RK stage, so that is
-            // the one timed (stage-2 coefficients, output into the stage
-            // buffers Q^(2) and its FP32 copy, which hold nothing between steps)
-            const bool rk = d == 2;
+            // zeta: the FP64 form's steps run the sweep with the fused RK
+            // stage, so that is the one timed (stage-2 coefficients, output
+            // into the stage buffer Q^(2), which holds nothing between steps);
+            // the mixed form's zeta sweep accumulates like eta
+            const bool rk = d == 2 && f64;
             for (int v = 0; v < kFluxVariants; ++v) {
                 const int cps = flux_ctas_per_sm(f64, d, v, visc, rk, ctx->cfg.scheme);
                 if (cps <= 0) continue;
@@ -439,7 +450,7 @@ int autotune(hx_ctx* ctx) {
                 a.fs = ctx->fs;
                 a.stress = ctx->grad;
                 a.A = ctx->A;
-                a.accumulate = 0;
+                a.accumulate = d > 0;
                 a.gas = ctx->gas;
                 a.scheme = ctx->cfg.scheme;
                 a.grid = (int)std::min<long long>(a.ntiles, (long long)cps * ctx->num_sms);
@@ -449,7 +460,7 @@ int autotune(hx_ctx* ctx) {
                     a.rk.Qk = ctx->Qn;
                     a.rk.metd = ctx->met;
                     a.rk.Qout = ctx->Qb;
-                    a.rk.Qfout = f64 ? nullptr : ctx->Qf[2];
+                    a.rk.Qfout = nullptr;
                     a.rk.Aref = ctx->Aref;
                     a.rk.ca = 0.75;
                     a.rk.cb = 0.25;
@@ -495,6 +506,7 @@ int autotune(hx_ctx* ctx) {
         if (cps <= 0) return fail(ctx, HX_ERR_CUDA, "the fused zeta sweep cannot launch on this device");
         ctx->grid_rk = (int)std::max<long long>(
             1, std::min<long long>(ctx->ntiles[2][ctx->variant[2]], (long long)cps * ctx->num_sms));
+        ctx->grid_z = ctx->grid[2];
     }
     ctx->tuned = true;
     return HX_OK;
@@ -953,7 +965,7 @@ int hx_finalize(hx_ctx* ctx) {
     ctx->n_bc = (int)bc.size();
     if ((rc = upload(ctx, &ctx->d_bc, bc))) return rc;
     HX_CK(cudaStreamSynchronize(ctx->stream));
-    ctx->launches_per_step = 3 * (1 + (visc ? 1 : 0) + 3 + (ctx->n_bc ? 1 : 0) +
+    ctx->launches_per_step = 3 * (1 + (visc ? 1 : 0) + 3 + (ctx->fp64() ? 0 : 1) + (ctx->n_bc ? 1 : 0) +
                                   (ctx->cfg.debug_poison ? (visc ? 4 : 2) : 0));
     ctx->finalized = true;
     return HX_OK;
