@@ -60,13 +60,25 @@ def stage_bytes_per_node(precision):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per interior node
-# of one launch of each sweep, from one ncu capture of the kernels whose
-# sources hash to TRAFFIC_SOURCES_SHA (mean over the three RK stages'
-# launches; profiles/ gives the command and the workload it was taken on).
-# Scaled to the benchmark's workload by its node count; null when the
-# kernel sources differ from the captured ones.
-TRAFFIC_SOURCES_SHA = None
-TRAFFIC_PER_NODE = {}
+# of one launch of each stage kernel, from one ncu capture of the kernels
+# whose sources hash to TRAFFIC_SOURCES_SHA: the 192^3 Taylor-Green block
+# (7,077,888 nodes) with the fixed tiles, the mean over the three RK
+# stages' launches (profiles/traffic_tgv192.md gives the command).  Scaled
+# to the benchmark's workload by its node count; null when the kernel
+# sources differ from the captured ones.
+TRAFFIC_SOURCES_SHA = "24d36bb431608674"
+TRAFFIC_PER_NODE = {
+    ("mixed", "prep"): 21.1, ("mixed", "stress"): 100.9, ("mixed", "flux_xi"): 96.2,
+    ("mixed", "flux_eta"): 115.6, ("mixed", "flux_zeta"): 139.2, ("mixed", "rk_stage"): 185.3,
+    ("fp64", "prep"): 87.7, ("fp64", "stress"): 200.9, ("fp64", "flux_xi"): 247.2,
+    ("fp64", "flux_eta"): 297.0, ("fp64", "flux_zeta_rk"): 335.7,
+}
+
+# Algorithmic work per node and RK stage besides the three sweeps: the
+# stress tensor (12 gradients by the sixth-order difference and the chain
+# rule, the stress and heat flux; about 200 flops), the primitives (10) and
+# the RK combination (30).
+STAGE_FLOPS_OTHER = 240
 
 
 def kernel_sources_sha():
@@ -207,53 +219,61 @@ def run_form(torch, hx, w, precision, steps, warmup, stream, dt, autotune=1):
     return e0.elapsed_time(e1) / 1e3, ctx
 
 
+def sweep_flops_per_node(name, precision, viscous):
+    """Algorithmic flops of one sweep launch per node (FP64: less the static
+    normals; the fused FP64 zeta sweep adds the RK combination)."""
+    f = FLUX_FLOPS_INV + (FLUX_FLOPS_VISC if viscous else 0)
+    if precision == "fp64":
+        f -= FLUX_FLOPS_STATIC_FP64
+    if name == "flux_zeta_rk":
+        f += RK_FLOPS
+    return f
+
+
 def roofline_for(ctx, w, precision, steps, dt, peaks, ms_per_step):
     """Per-kernel CUDA-event durations of `steps` launch-by-launch steps of
-    the same workload on the same stream; roofline of the dominant kernel.
-    Its algorithmic bytes are the whole stage's (stage_bytes_per_node x the
-    nodes one launch updates: the fused zeta sweep finishes the stage), its
-    algorithmic flops those of one sweep; the bound reported is the larger
-    fraction (FP64: the FP64 pipe).  stage_view divides the same bytes by the
-    mean graph-replayed stage time."""
+    the same workload on the same stream, and the roofline of the dominant
+    kernel.  A flux sweep is bound by its arithmetic (FP64 pipe; FP32 issue
+    in the mixed form): achieved = its algorithmic flops per launch / launch
+    time against the FMA peak measured in this run; a point kernel by HBM.
+    hbm_view: the stage's algorithmic bytes (stage_bytes_per_node x nodes)
+    over this launch's time; traffic_view: the kernel's measured DRAM bytes
+    over its time; stage_view: the stage's bytes and flops over the mean
+    graph-replayed stage time."""
     stats = ctx.profile_step(steps, dt)
     name, (launches, tot) = max(stats.items(), key=lambda kv: kv[1][1])
     per_launch_s = tot / launches / 1e3
     npts = w.npts
     out = {"kernel": name, "launch_ms": tot / launches, "share": tot / sum(v[1] for v in stats.values())}
+    alu_peak = peaks["fp64_tflops"] if precision == "fp64" else peaks["fp32_tflops"]
+    alu_src = "%s FMA, %s" % ("FP64" if precision == "fp64" else "FP32", peaks["alu_src"])
     bytes_ = stage_bytes_per_node(precision) * npts
-    gbs = bytes_ / per_launch_s / 1e9
-    hbm_frac = gbs / peaks["hbm_gbs"]
-    stage_s = ms_per_step / 3.0 / 1e3
-    stage_view = {"achieved": bytes_ / stage_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                  "frac": bytes_ / stage_s / 1e9 / peaks["hbm_gbs"], "stage_ms": stage_s * 1e3,
-                  "bytes_per_node": stage_bytes_per_node(precision)}
+    hbm = {"achieved": bytes_ / per_launch_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": bytes_ / per_launch_s / 1e9 / peaks["hbm_gbs"], "peak_src": peaks["src"],
+           "note": "the whole stage's algorithmic bytes over this launch"}
     if name.startswith("flux_"):
-        flops = (FLUX_FLOPS_INV + (FLUX_FLOPS_VISC if w.viscous else 0)) * npts
-        if precision == "fp64":
-            flops -= FLUX_FLOPS_STATIC_FP64 * npts
-        if name == "flux_zeta_rk":
-            flops += RK_FLOPS * npts
-        tfl = flops / per_launch_s / 1e12
-        alu_peak = peaks["fp64_tflops"] if precision == "fp64" else peaks["fp32_tflops"]
-        alu_frac = tfl / alu_peak
-        alu = {"achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
-               "peak_src": "%s FMA, %s" % ("FP64" if precision == "fp64" else "FP32", peaks["alu_src"])}
-        hbm = {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
-               "peak_src": peaks["src"]}
-        if precision == "fp64" or alu_frac >= hbm_frac:
-            out.update({"bound": "alu", **alu, "hbm_view": hbm})
-        else:
-            out.update({"bound": "hbm", **hbm, "alu_view": alu})
+        tfl = sweep_flops_per_node(name, precision, w.viscous) * npts / per_launch_s / 1e12
+        out.update({"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
+                    "peak_src": alu_src, "hbm_view": hbm})
     else:
-        out.update({"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
-                    "peak_src": peaks["src"]})
-    out["stage_view"] = stage_view
+        out.update({"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s",
+                    "frac": hbm["frac"], "peak_src": peaks["src"]})
+    stage_s = ms_per_step / 3.0 / 1e3
+    stage_flops = (3 * sweep_flops_per_node("flux_xi", precision, w.viscous) + STAGE_FLOPS_OTHER) * npts
+    out["stage_view"] = {"stage_ms": stage_s * 1e3, "bytes_per_node": stage_bytes_per_node(precision),
+                         "hbm_achieved": bytes_ / stage_s / 1e9, "hbm_frac": bytes_ / stage_s / 1e9 / peaks["hbm_gbs"],
+                         "flops_per_node": stage_flops / npts, "alu_achieved": stage_flops / stage_s / 1e12,
+                         "alu_frac": stage_flops / stage_s / 1e12 / alu_peak}
     sha = kernel_sources_sha()
     per_node = TRAFFIC_PER_NODE.get((precision, name)) if sha == TRAFFIC_SOURCES_SHA else None
     out["traffic"] = per_node * npts if per_node is not None else None
-    out["traffic_src"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, %.1f B per node scaled "
-                          "by the nodes (profiles/)" % per_node) if per_node is not None else \
-        "null: no ncu capture of kernel sources %s" % sha
+    if per_node is not None:
+        out["traffic_src"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, %.1f B per node on "
+                              "192^3 scaled by the nodes (profiles/traffic_tgv192.md)" % per_node)
+        out["traffic_view"] = {"achieved": per_node * npts / per_launch_s / 1e9, "unit": "GB/s",
+                               "frac": per_node * npts / per_launch_s / 1e9 / peaks["hbm_gbs"]}
+    else:
+        out["traffic_src"] = "null: no ncu capture of kernel sources %s" % sha
     out["per_kernel_ms"] = {k: v[1] / v[0] for k, v in stats.items()}
     out["autotune"] = ctx.tuning()
     return out

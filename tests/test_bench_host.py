@@ -65,7 +65,12 @@ def test_traffic_is_null_unless_the_sources_match(monkeypatch):
     monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA", sha)
     out = bench.roofline_for(Ctx(), Wl(), "fp64", 2, 1e-3, peaks, 9.0)
     assert out["traffic"] == pytest.approx(100.0 * 1000)
+    assert out["traffic_view"]["achieved"] == pytest.approx(100.0 * 1000 / 1e-3 / 1e9)
     # achieved flops per launch over the launch time (1 ms)
     flops = (bench.FLUX_FLOPS_INV + bench.FLUX_FLOPS_VISC - bench.FLUX_FLOPS_STATIC_FP64) * 1000
     assert out["achieved"] == pytest.approx(flops / 1e-3 / 1e12)
+    assert out["frac"] == pytest.approx(out["achieved"] / 1.0)
+    # the stage's algorithmic bytes over this launch, and over the stage
+    assert out["hbm_view"]["achieved"] == pytest.approx(bench.stage_bytes_per_node("fp64") * 1000 / 1e-3 / 1e9)
     assert out["stage_view"]["stage_ms"] == pytest.approx(3.0)
+    assert out["stage_view"]["hbm_achieved"] == pytest.approx(bench.stage_bytes_per_node("fp64") * 1000 / 3e-3 / 1e9)
