@@ -553,54 +553,105 @@ k_grad(const Brick* __restrict__ cols, int nb, const DevBlock* __restrict__ bloc
 // kernel instead of trailing the stencil phases of the zeta sweep, and the
 // format conversions run on the integer pipe (widen_f32, narrow_f64_rn), so
 // that the FP64 unit does only the ten FMAs of the combination.
-__global__ void __launch_bounds__(kThreads, 4)
+// Each thread owns two i-adjacent nodes of a 32 x 8 brick (an aligned
+// 8-byte pair of every FP32 field, a 16-byte pair of every FP64 one), so the
+// stage's loads and stores are vector accesses.
+constexpr int kRkThreads = 128;
+
+__global__ void __launch_bounds__(kRkThreads, 6)
 k_rk_stage(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ blocks, const float* __restrict__ A,
            const float* __restrict__ metf, long long fs, GasR<float> gs, RKArgs rk) {
+    const int ti = 2 * (threadIdx.x & 15), tj = threadIdx.x >> 4;
     for (int t = blockIdx.x; t < nb; t += gridDim.x) {
         const Brick br = bricks[t];
-        int i, j, k;
-        bool ok;
-        brick_node(br, i, j, k, ok);
-        if (!ok) continue;
+        if (ti >= br.ni || tj >= br.nj) continue;
+        const bool two = ti + 1 < br.ni;   // the pair's second node lies in the brick
+        const int i = br.i0 + ti, j = br.j0 + tj, k = br.k0;
         const DevBlock& B = blocks[br.b];
-        const long long e = node_index(B, i, j, k);
-        float dv[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) dv[c] = rk.Aref ? A[c * fs + e] - rk.Aref[c * fs + e] : A[c * fs + e];
-        const float fr = rk.ccf * narrow_f64_rn(rk.dtl ? rk.dtl[e] : B.dt) * metf[9 * fs + e];
-        double qo[5];
+        const long long e = node_index(B, i, j, k);   // even: i is even and rows start on 8-element boundaries
+        float2 dv[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-            const double r = widen_f32(fr * dv[c]);
-            qo[c] = fma(rk.ca, rk.Qn[c * fs + e], rk.cb != 0.0 ? fma(rk.cb, rk.Qk[c * fs + e], r) : r);
-        }
-        if (B.wall) {
-            const bool on = ((B.wall & 1) && i == 0) || ((B.wall & 2) && i == B.n[0] - 1) ||
-                            ((B.wall & 4) && j == 0) || ((B.wall & 8) && j == B.n[1] - 1) ||
-                            ((B.wall & 16) && k == 0) || ((B.wall & 32) && k == B.n[2] - 1);
-            if (on) {
-                const double pw = rk.gm1 * (qo[4] - 0.5 * (qo[1] * qo[1] + qo[2] * qo[2] + qo[3] * qo[3]) / qo[0]);
-                qo[1] = qo[2] = qo[3] = 0.0;
-                qo[4] = pw / rk.gm1;
+            dv[c] = *reinterpret_cast<const float2*>(A + c * fs + e);
+            if (rk.Aref) {
+                const float2 r = *reinterpret_cast<const float2*>(rk.Aref + c * fs + e);
+                dv[c].x -= r.x;
+                dv[c].y -= r.y;
             }
         }
-        bool bad = false;
-        float qv[5];
+        const float2 J = *reinterpret_cast<const float2*>(metf + 9 * fs + e);
+        double qo[2][5];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const float fr = rk.ccf * narrow_f64_rn(rk.dtl ? rk.dtl[e + l] : B.dt) * (l ? J.y : J.x);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) qo[l][c] = widen_f32(fr * (l ? dv[c].y : dv[c].x));
+        }
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-            bad = bad || nonfinite_bits(qo[c]);
-            rk.Qout[c * fs + e] = qo[c];
-            qv[c] = narrow_f64_rn(qo[c]);
-            rk.Qfout[c * fs + e] = qv[c];
+            const double2 qn = *reinterpret_cast<const double2*>(rk.Qn + c * fs + e);
+            if (rk.cb != 0.0) {
+                const double2 qk = *reinterpret_cast<const double2*>(rk.Qk + c * fs + e);
+                qo[0][c] = fma(rk.ca, qn.x, fma(rk.cb, qk.x, qo[0][c]));
+                qo[1][c] = fma(rk.ca, qn.y, fma(rk.cb, qk.y, qo[1][c]));
+            } else {
+                qo[0][c] = fma(rk.ca, qn.x, qo[0][c]);
+                qo[1][c] = fma(rk.ca, qn.y, qo[1][c]);
+            }
+        }
+        if (B.wall) {
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const int il = i + l;
+                const bool on = ((B.wall & 1) && il == 0) || ((B.wall & 2) && il == B.n[0] - 1) ||
+                                ((B.wall & 4) && j == 0) || ((B.wall & 8) && j == B.n[1] - 1) ||
+                                ((B.wall & 16) && k == 0) || ((B.wall & 32) && k == B.n[2] - 1);
+                if (on) {
+                    double* q = qo[l];
+                    const double pw = rk.gm1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+                    q[1] = q[2] = q[3] = 0.0;
+                    q[4] = pw / rk.gm1;
+                }
+            }
+        }
+        float qv[2][5];
+        bool bad = false, unphys = false;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            if (l == 1 && !two) break;
+            bool b = false;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                b = b || nonfinite_bits(qo[l][c]);
+                qv[l][c] = narrow_f64_rn(qo[l][c]);
+            }
+            const float* v = qv[l];
+            unphys = unphys || (!b && !(v[0] > 0.0f && v[4] * v[0] - 0.5f * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) > 0.0f));
+            bad = bad || b;
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            if (two) {
+                *reinterpret_cast<double2*>(rk.Qout + c * fs + e) = make_double2(qo[0][c], qo[1][c]);
+                *reinterpret_cast<float2*>(rk.Qfout + c * fs + e) = make_float2(qv[0][c], qv[1][c]);
+            } else {
+                rk.Qout[c * fs + e] = qo[0][c];
+                rk.Qfout[c * fs + e] = qv[0][c];
+            }
         }
         if (rk.primout) {   // the next stage's primitives, from the FP32 copy as in k_prep
-            float pv[4];
-            primitives(gs, qv, pv);
+            float pv[2][4];
+            primitives(gs, qv[0], pv[0]);
+            if (two) primitives(gs, qv[1], pv[1]);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) rk.primout[c * fs + e] = pv[c];
+            for (int c = 0; c < 4; ++c) {
+                if (two)
+                    *reinterpret_cast<float2*>(rk.primout + c * fs + e) = make_float2(pv[0][c], pv[1][c]);
+                else
+                    rk.primout[c * fs + e] = pv[0][c];
+            }
         }
-        if (!bad && !(qv[0] > 0.0f && qv[4] * qv[0] - 0.5f * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]) > 0.0f))
-            atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
+        if (unphys) atomicOr(rk.flags, (unsigned)FLAG_UNPHYSICAL);
         if (bad) atomicOr(rk.flags, (unsigned)FLAG_NONFINITE);
     }
 }
@@ -905,7 +956,8 @@ cudaError_t launch_rk_stage(const Brick* bricks, int nb, const DevBlock* blocks,
     if (nb <= 0) return cudaSuccess;
     GasR<float> gs;
     gs.init(gas);
-    k_rk_stage<<<grid_for((long long)nb * kThreads), kThreads, 0, s>>>(bricks, nb, blocks, A, metf, fs, gs, rk);
+    k_rk_stage<<<grid_for((long long)nb * kRkThreads, kRkThreads), kRkThreads, 0, s>>>(bricks, nb, blocks, A, metf,
+                                                                                          fs, gs, rk);
     return cudaGetLastError();
 }
 
