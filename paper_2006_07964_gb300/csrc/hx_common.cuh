@@ -254,9 +254,12 @@ __device__ __forceinline__ float hmin0(float x) { return fminf(x, 0.0f); }
 template <class R>
 struct GasR {   // gas constants in the working precision (built on the host)
     R gamma, gm1, inv_2gamma, two_gm1, mach_re, kq_fac, suth, one_p_suth, inv_gm1;
+    R gm1_over_g, inv_g_sqrt2;   // (gamma-1)/gamma and 1/(gamma sqrt 2): a node's own characteristic values
     int mu_law;
     __host__ __device__ void init(const Gas& g) {
         gamma = R(g.gamma);
+        gm1_over_g = R((g.gamma - 1.0) / g.gamma);
+        inv_g_sqrt2 = R(0.70710678118654752440 / g.gamma);
         gm1 = R(g.gamma - 1.0);
         inv_2gamma = R(1.0 / (2.0 * g.gamma));
         two_gm1 = R(2.0 * (g.gamma - 1.0));
@@ -574,6 +577,16 @@ struct CharBasis {
         const R imm = hrsqrt(mx * mx + my * my + mz * mz);
         set_normal(mx * imm, my * imm, mz * imm);
     }
+    // W = L q of the node's own state q: there d = 0 and
+    // S = rho - p/c^2 = rho (gamma-1)/gamma, so W_0..2 = k rho (gamma-1)/gamma
+    // and W_3 = W_4 = c/(gamma sqrt 2) (equal to project() up to rounding).
+    __device__ __forceinline__ void center(const GasR<R>& gs, R W[5]) const {
+        const R S = rho * gs.gm1_over_g;
+        W[0] = kx * S;
+        W[1] = ky * S;
+        W[2] = kz * S;
+        W[3] = W[4] = c * gs.inv_g_sqrt2;
+    }
     // W = L q
     __device__ __forceinline__ void project(R q0, R q1, R q2, R q3, R q4, R W[5]) const {
         const R d1 = q1 - u * q0, d2 = q2 - v * q0, d3 = q3 - w * q0;
@@ -635,6 +648,14 @@ struct CharBasis<float> {
         init_state(gs, q);
         const R imm = hrsqrt(mx * mx + my * my + mz * mz);
         set_normal(mx * imm, my * imm, mz * imm);
+    }
+    // W = L q of the node's own state (as CharBasis<double>::center)
+    __device__ __forceinline__ void center(const GasR<R>& gs, R W[5]) const {
+        const R S = rho * gs.gm1_over_g;
+        W[0] = kx * S;
+        W[1] = ky * S;
+        W[2] = kz * S;
+        W[3] = W[4] = c * gs.inv_g_sqrt2;
     }
     // W = L q
     __device__ __forceinline__ void project(R q0, R q1, R q2, R q3, R q4, R W[5]) const {
@@ -703,8 +724,7 @@ __device__ __forceinline__ float hneg(float x) {
 //   H = |u|^2/2 + c^2/(gamma-1): the energy row's (|u|^2+c^2)/2 and
 //   (3-gamma) c^2 / (2 (gamma-1)) terms of (l4+l5) sum to H.
 template <class R, bool POS>
-__device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R kx, R ky, R kz, R mm, R F[5]) {
-    const R irho = hrcp(q[0]);
+__device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R irho, R kx, R ky, R kz, R mm, R F[5]) {
     const R u = q[1] * irho, v = q[2] * irho, w = q[3] * irho;
     const R uu = u * u + v * v + w * w;
     const R p = gs.gm1 * (q[4] - R(0.5) * q[0] * uu);
@@ -731,6 +751,28 @@ __device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R kx, R
     F[2] = v * aM + ky * acD;
     F[3] = w * aM + kz * acD;
     F[4] = a * (gs.gm1 * l1 * uu + S45 * H) + th * acD;
+}
+
+// h = F+(ql) + F-(qr) of a face along (kx, ky, kz) * mm.  In FP64 the two
+// densities share one division: 1/rho_l = rho_r / (rho_l rho_r) and
+// 1/rho_r = rho_l / (rho_l rho_r).
+template <class R>
+__device__ __forceinline__ void face_flux(const GasR<R>& gs, const R ql[5], const R qr[5], R kx, R ky, R kz, R mm,
+                                          R h[5]) {
+    R il, ir;
+    if (sizeof(R) == 8) {
+        const R inv = hrcp(ql[0] * qr[0]);
+        il = qr[0] * inv;
+        ir = ql[0] * inv;
+    } else {
+        il = hrcp(ql[0]);
+        ir = hrcp(qr[0]);
+    }
+    R Fp[5], Fm[5];
+    sw_flux<R, true>(gs, ql, il, kx, ky, kz, mm, Fp);
+    sw_flux<R, false>(gs, qr, ir, kx, ky, kz, mm, Fm);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) h[k] = Fp[k] + Fm[k];
 }
 
 // Stress tensor and work + heat-flux vector at a node, Eqs. (5)-(6) and the

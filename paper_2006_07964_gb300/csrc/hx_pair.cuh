@@ -116,6 +116,14 @@ struct CharBasisP {
         kz = mz * imm;
         cth = c * pfma(kx, u, pfma(ky, v, kz * w));
     }
+    // W = L q of the node's own state (as CharBasis<double>::center)
+    __device__ __forceinline__ void center(const GasR<float>& gs, P2 W[5]) const {
+        const P2 S = rho * pk(gs.gm1_over_g);
+        W[0] = kx * S;
+        W[1] = ky * S;
+        W[2] = kz * S;
+        W[3] = W[4] = c * pk(gs.inv_g_sqrt2);
+    }
     // W = L q
     __device__ __forceinline__ void project(P2 q0, P2 q1, P2 q2, P2 q3, P2 q4, P2 W[5]) const {
         const P2 d1 = (q1 - u * q0) * irho, d2 = (q2 - v * q0) * irho, d3 = (q3 - w * q0) * irho;

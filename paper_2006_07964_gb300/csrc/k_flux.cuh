@@ -245,6 +245,10 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     R W[5][5];
 #pragma unroll
                     for (int s = -2; s <= 2; ++s) {
+                        if (s == 0) {   // the node's own state: closed form
+                            cb.center(gs, W[2]);
+                            continue;
+                        }
                         const int si = LY::idx(p + s, a);
                         cb.project(sQ[si], sQ[PL + si], sQ[2 * PL + si], sQ[3 * PL + si], sQ[4 * PL + si], W[s + 2]);
                     }
@@ -291,7 +295,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         ky = mf[1] * imm;
                         kz = mf[2] * imm;
                     }
-                    R ql[5], qr[5], Fp[5], Fm[5];
+                    R ql[5], qr[5];
                     if (SCH == 0) {
 #pragma unroll
                         for (int k = 0; k < 5; ++k) {
@@ -317,10 +321,10 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         cb.back(WL, ql);
                         cb.back(WR, qr);
                     }
-                    sw_flux<R, true>(gs, ql, kx, ky, kz, mm, Fp);
-                    sw_flux<R, false>(gs, qr, kx, ky, kz, mm, Fm);
+                    R h[5];
+                    face_flux(gs, ql, qr, kx, ky, kz, mm, h);
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) sUL[k * PL + uf] = Fp[k] + Fm[k];
+                    for (int k = 0; k < 5; ++k) sUL[k * PL + uf] = h[k];
                 }
             }
             __syncthreads();

@@ -199,6 +199,10 @@ k_flux2(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int
                     P2 W[5][5];
 #pragma unroll
                     for (int s = -2; s <= 2; ++s) {
+                        if (s == 0) {   // the node's own state: closed form
+                            cb.center(gs, W[2]);
+                            continue;
+                        }
                         const int si = LY::idx(p + s, a2);
                         cb.project(ld2(sQ + si), ld2(sQ + PL + si), ld2(sQ + 2 * PL + si), ld2(sQ + 3 * PL + si),
                                    ld2(sQ + 4 * PL + si), W[s + 2]);
