@@ -602,6 +602,8 @@ def main():
         ectx.set_state(b, hq[b].numpy())
     ectx.step(1, dt)
     torch.cuda.synchronize()
+    eclocks = Clocks(local)
+    eclocks.start()
     t0 = time.perf_counter()
     for _ in range(e_steps):
         for b in range(len(w.blocks)):
@@ -609,10 +611,12 @@ def main():
         ectx.step(1, dt)
         for b in range(len(w.blocks)):
             ectx.get_state(b, hout[b].numpy())
-    e_secs = max_over_ranks(time.perf_counter() - t0)
+    e_secs = time.perf_counter() - t0
+    eck = eclocks.stop()
+    e_secs = max_over_ranks(e_secs)
     ectx.close()
     e2e = {"value": ranks.throughput(w.npts, e_steps, e_secs), "unit": "Mpts/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": h2d, "steps": e_steps}
+           "d2h_bytes_per_step": h2d, "steps": e_steps, "clocks": eck}
 
     if rank != 0:
         return
