@@ -37,8 +37,9 @@ struct FluxLayout {
     // (i), planes [slot][line].
     static constexpr int PLANE = RING * NA;
     // fields per ring slot: Q 5, metric 3, node flux 5, U^L (then h) 5, U^R 5, viscous node flux 4;
-    // FP64 adds the stored unit normals of the node (3) and of its + face (4)
-    static constexpr int NF_INV = 23, NF_VISC = 27, NF_NRM = 7;
+    // with stored normals (NRM) the metric and the normals are read at the
+    // node and face that use them, not staged: 3 fields fewer
+    static constexpr int NF_INV = 23, NF_VISC = 27;
     static_assert((NA & (NA - 1)) == 0 && (TP & (TP - 1)) == 0 && (RING & (RING - 1)) == 0,
                   "power-of-two line count, chunk and ring");
     // Slot of node p: (p mod RING); DIR 0 rotates odd lines by RING/2 (the
@@ -67,9 +68,9 @@ struct FluxLayout {
             p = (int)(u / NA);
         }
     }
-    template <class R, bool VISC>
+    template <class R, bool VISC, bool NRM>
     static constexpr size_t smem_bytes() {
-        return sizeof(R) * (size_t)PLANE * ((VISC ? NF_VISC : NF_INV) + (sizeof(R) == 8 ? NF_NRM : 0));
+        return sizeof(R) * (size_t)PLANE * ((VISC ? NF_VISC : NF_INV) - (NRM ? 3 : 0));
     }
 };
 
@@ -80,21 +81,24 @@ struct FluxLayout {
 // SCH 0: modified AFWENO (characteristic space at the node, Figs. 10-11);
 // SCH 1: original AFWENO (characteristic space at the face from the mean
 // state and the face metric, two independent WENOs per face, Fig. 9).
+// NRM (FP64 with the stored unit normals of k_normals): the node basis and
+// the face metric are read from them instead of formed from the metric.
 // Resident CTAs per SM that the register allocation must allow.  FP64: two
 // of 256 threads (128 registers) or three of 128, so that the FP64 pipe
-// always has a second CTA's warps.  FP32 Navier-Stokes with 128 threads:
+// always has a second CTA's warps (four of 128 spill at 128 registers and
+// measured 1.3 % slower).  FP32 Navier-Stokes with 128 threads:
 // seven (72 registers), which is what its shared memory allows; left free,
 // the allocation drifts between 72 and 80 registers (six CTAs) with small
 // code changes.  Other FP32 sweeps: no target (0); the compiler's own
 // allocation measured as fast as a 64-register target and faster than an
 // explicit 85-register one, and Euler sweeps keep 56-64 registers.
-template <class R, int NT, bool VISC>
+template <class R, int NT, bool VISC, bool NRM>
 constexpr int flux_min_ctas() {
     return sizeof(R) == 8 ? (NT >= 256 ? 2 : 3) : (VISC && NT < 256 ? 7 : 0);
 }
 
-template <class R, int DIR, int TP, int NA, bool VISC, bool RK, int SCH>
-__global__ void __launch_bounds__(TP * NA, flux_min_ctas<R, TP * NA, VISC>())
+template <class R, int DIR, int TP, int NA, bool VISC, bool RK, int SCH, bool NRM>
+__global__ void __launch_bounds__(TP * NA, flux_min_ctas<R, TP * NA, VISC, NRM>())
 k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int ntiles,
        const R* __restrict__ Q, const R* __restrict__ met, const R* __restrict__ nrm, long long fs,
        const R* __restrict__ stress, R* __restrict__ A, int accumulate, GasR<R> gs, RKArgs rk) {
@@ -102,17 +106,13 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
     constexpr int PL = LY::PLANE;
     constexpr int NT = TP * NA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    static_assert(!NRM || sizeof(R) == 8, "stored normals are the FP64 form's");
     R* sQ = reinterpret_cast<R*>(smem_raw);   // 5 planes
-    R* sM = sQ + 5 * PL;                       // 3
-    R* sF = sM + 3 * PL;                       // 5
+    R* sM = sQ + 5 * PL;                       // 3 (not NRM)
+    R* sF = sM + (NRM ? 0 : 3) * PL;           // 5
     R* sUL = sF + 5 * PL;                      // 5 (U^L at the + face, then h)
     R* sUR = sUL + 5 * PL;                     // 5 (U^R at the - face)
     R* sFv = sUR + 5 * PL;                     // 4 (VISC)
-    R* sKn = sFv + (VISC ? 4 : 0) * PL;        // 3 (FP64): node unit normal
-    R* sKf = sKn + 3 * PL;                     // 4 (FP64): + face unit normal and |m|
-    // FP64 with stored normals (static grid data, k_normals): the node basis
-    // and the face metric are read instead of formed from the metric
-    const bool pre = sizeof(R) == 8 && nrm != nullptr;
     const int tid = threadIdx.x;
 
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -140,16 +140,9 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     const int s = LY::idx(p, a);
 #pragma unroll
                     for (int f = 0; f < 5; ++f) sQ[f * PL + s] = Q[f * fs + e];
+                    if (!NRM) {
 #pragma unroll
-                    for (int f = 0; f < 3; ++f) sM[f * PL + s] = met[(3 * DIR + f) * fs + e];
-                    if (pre && p >= -1 && p <= n) {
-                        const R* nr = nrm + 7 * DIR * fs + e;
-#pragma unroll
-                        for (int f = 0; f < 3; ++f) sKn[f * PL + s] = nr[f * fs];
-                        if (p <= n - 1) {
-#pragma unroll
-                            for (int f = 0; f < 4; ++f) sKf[f * PL + s] = nr[(3 + f) * fs];
-                        }
+                        for (int f = 0; f < 3; ++f) sM[f * PL + s] = met[(3 * DIR + f) * fs + e];
                     }
                 }
             }
@@ -202,18 +195,27 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     if (a0 + a >= na || p > n + 2) continue;
                     const int s0 = LY::idx(p, a);
                     const bool vnode = VISC && !((lo && p < 0) || (hi && p >= n));
+                    const long long e = hx_chk(B, e0 + p * sd + a * sa);
                     R S[9];
                     if (vnode) {   // issued first; consumed after the node flux
-                        const long long e = hx_chk(B, e0 + p * sd + a * sa);
 #pragma unroll
                         for (int f = 0; f < 9; ++f) S[f] = stress[f * fs + e];
                     }
                     R q[5];
 #pragma unroll
                     for (int f = 0; f < 5; ++f) q[f] = sQ[f * PL + s0];
-                    const R mx = sM[s0], my = sM[PL + s0], mz = sM[2 * PL + s0];
+                    R mx, my, mz;
+                    if (NRM) {
+                        mx = met[(3 * DIR) * fs + e];
+                        my = met[(3 * DIR + 1) * fs + e];
+                        mz = met[(3 * DIR + 2) * fs + e];
+                    } else {
+                        mx = sM[s0];
+                        my = sM[PL + s0];
+                        mz = sM[2 * PL + s0];
+                    }
                     CharBasis<R> cb;
-                    if (pre)
+                    if (NRM)
                         cb.init_state(gs, q);
                     else
                         cb.init(gs, q, mx, my, mz);
@@ -241,7 +243,10 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         if (LATE_FV) put_fv();
                         continue;
                     }
-                    if (pre) cb.set_normal(sKn[s0], sKn[PL + s0], sKn[2 * PL + s0]);
+                    if (NRM) {   // node normal (defined on nodes -1 .. n)
+                        const R* nr = nrm + 7 * DIR * fs + e;
+                        cb.set_normal(nr[0], nr[fs], nr[2 * fs]);
+                    }
                     R W[5][5];
 #pragma unroll
                     for (int s = -2; s <= 2; ++s) {
@@ -275,11 +280,12 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     if (a0 + a >= na || f > n - 1) continue;
                     const int uf = LY::idx(f, a), ur = LY::idx(f + 1, a);
                     R kx, ky, kz, mm;
-                    if (pre) {
-                        kx = sKf[uf];
-                        ky = sKf[PL + uf];
-                        kz = sKf[2 * PL + uf];
-                        mm = sKf[3 * PL + uf];
+                    if (NRM) {   // + face normal and |m| of node f (defined on nodes -1 .. n-1)
+                        const R* nr = nrm + (7 * DIR + 3) * fs + hx_chk(B, e0 + f * sd + a * sa);
+                        kx = nr[0];
+                        ky = nr[fs];
+                        kz = nr[2 * fs];
+                        mm = nr[3 * fs];
                     } else {
                         R mf[3];
 #pragma unroll

@@ -22,28 +22,40 @@ namespace {
 // The mixed form's sweeps of the modified scheme (FP32, SCH 0) run the
 // two-lines-per-thread kernel of k_flux2.cuh (TP x NA/2 threads); the FP64
 // form and the original scheme run k_flux.  Only the FP64 form fuses the RK
-// stage into its zeta sweep.
+// stage into its zeta sweep.  FP64 contexts read the sweeps' stored unit
+// normals (NRM); a call without them (the allocation-free Euler residual)
+// runs the FP64 Euler sweep that forms them from the metric.
 template <class R, int DIR, int V, bool VISC, bool RK = false, int SCH = 0>
 struct FluxInst {
     static constexpr int TP = flux_tp(DIR, V), NA = flux_na(DIR, V);
     static constexpr bool PAIR = std::is_same<R, float>::value && SCH == 0;
-    static_assert(!RK || std::is_same<R, double>::value, "the fused RK stage is the FP64 form's");
+    static constexpr bool F64 = std::is_same<R, double>::value;
+    static constexpr bool PLAIN64 = F64 && !VISC && !RK && SCH == 0;   // FP64 without stored normals exists
+    static_assert(!RK || F64, "the fused RK stage is the FP64 form's");
     static constexpr int NT = PAIR ? TP * NA / 2 : TP * NA;
     static constexpr size_t smem = PAIR ? Flux2Layout<DIR, TP, NA / 2>::smem_bytes(VISC)
-                                        : FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC>();
+                                        : FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC, F64>();
+    static constexpr size_t smem_plain = FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC, false>();
     static auto kernel() {
         if constexpr (PAIR)
             return k_flux2<DIR, TP, NA / 2, VISC>;
         else
-            return k_flux<R, DIR, TP, NA, VISC, RK, SCH>;
+            return k_flux<R, DIR, TP, NA, VISC, RK, SCH, F64>;
+    }
+    static bool opt_in(const void* kern, size_t bytes) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
     }
     static int ctas() {
         auto kern = kernel();
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-            cudaGetLastError();
-            return 0;
+        if constexpr (PLAIN64) {
+            if (!opt_in((const void*)k_flux<R, DIR, TP, NA, VISC, RK, SCH, false>, smem_plain)) return 0;
         }
+        if (!opt_in((const void*)kern, smem)) return 0;
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) != cudaSuccess) {
             cudaGetLastError();
@@ -54,14 +66,27 @@ struct FluxInst {
     static cudaError_t run(const FluxArgs& a, cudaStream_t s) {
         GasR<R> gs;
         gs.init(a.gas);
-        if constexpr (PAIR)
+        if constexpr (PAIR) {
             k_flux2<DIR, TP, NA / 2, VISC><<<a.grid, NT, smem, s>>>(
                 a.blocks, a.tiles, a.ntiles, (const float*)a.Q, (const float*)a.met, a.fs, (const float*)a.stress,
                 (float*)a.A, a.accumulate, gs);
-        else
-            k_flux<R, DIR, TP, NA, VISC, RK, SCH><<<a.grid, NT, smem, s>>>(
-                a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, (const R*)a.nrm, a.fs,
-                (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
+        } else if constexpr (F64) {
+            if (a.nrm) {
+                k_flux<R, DIR, TP, NA, VISC, RK, SCH, true><<<a.grid, NT, smem, s>>>(
+                    a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, (const R*)a.nrm, a.fs,
+                    (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
+            } else if constexpr (PLAIN64) {
+                k_flux<R, DIR, TP, NA, VISC, RK, SCH, false><<<a.grid, NT, smem_plain, s>>>(
+                    a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, nullptr, a.fs, (const R*)a.stress,
+                    (R*)a.A, a.accumulate, gs, a.rk);
+            } else {
+                return cudaErrorInvalidValue;   // FP64 sweeps other than the Euler one need the stored normals
+            }
+        } else {
+            k_flux<R, DIR, TP, NA, VISC, RK, SCH, false><<<a.grid, NT, smem, s>>>(
+                a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, nullptr, a.fs, (const R*)a.stress,
+                (R*)a.A, a.accumulate, gs, a.rk);
+        }
         return cudaGetLastError();
     }
 };
