@@ -421,11 +421,11 @@ k_prim(const Brick* __restrict__ bricks, int nb, const DevBlock* __restrict__ bl
 // halo nodes along i and j (the i and j derivatives; corners are never
 // read).  A node's primitives are read about twice from global memory
 // (own column once, halos of the neighbouring tiles) instead of 19 times.
-// Register targets: two CTAs per SM in FP32 (128 registers), one in FP64.
+// Register target: two CTAs per SM (128 registers).
 constexpr int kColX = 32, kColY = 8;
 
 template <class R, bool STRESS>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, 2)
 k_grad(const Brick* __restrict__ cols, int nb, const DevBlock* __restrict__ blocks, const R* __restrict__ prim,
        const R* __restrict__ met, long long fs, R* __restrict__ out, GasR<R> gs) {
     __shared__ R sp[4][kColY + 6][kColX + 6];
@@ -485,9 +485,13 @@ k_grad(const Brick* __restrict__ cols, int nb, const DevBlock* __restrict__ bloc
                 for (int v = 0; v < 4; ++v) qv[s][v] = prim[v * fs + e];
             }
         }
-        fetch(br.k0);
+        // FP32 loads a plane ahead; FP64, bound by its FP64 pipe, loads the
+        // plane at the top of its step and keeps the registers for two CTAs
+        constexpr bool AHEAD = sizeof(R) == 4;
+        if (AHEAD) fetch(br.k0);
         for (int kk = 0; kk < br.nk; ++kk) {
             const int k = br.k0 + kk;
+            if (!AHEAD) fetch(k);
             R m[10];
 #pragma unroll
             for (int s = 0; s < 6; ++s)
@@ -507,7 +511,7 @@ k_grad(const Brick* __restrict__ cols, int nb, const DevBlock* __restrict__ bloc
                 for (int v = 0; v < 4; ++v) sp[v][hy_ + 3][hx_ + 3] = nh[v];
             }
             __syncthreads();
-            if (kk + 1 < br.nk) fetch(k + 1);
+            if (AHEAD && kk + 1 < br.nk) fetch(k + 1);
             if (!own) continue;
             const long long e = node_index(B, i, j, k);
             R dc[4][3];
