@@ -145,6 +145,9 @@ CASES = {
     "ogrid_s8": lambda: W.ogrid(scale=8),
     "shock_warped": lambda: W.shocktube((96, 12, 12), amp=0.04),
     "shock_vortex": lambda: W.shock_vortex((64, 32, 8), amp=0.04),
+    # long lines and few line groups (a sweep CTA marches 200-256 nodes)
+    "long_xi_ns": lambda: warped((200, 12, 10), viscous=True, reynolds=100.0),
+    "long_zeta_euler": lambda: warped((12, 10, 256)),
     "tiny_ns3": lambda: split(warped((24, 8, 8), viscous=True, reynolds=50.0), (3, 1, 1)),
     "min6": lambda: warped((6, 6, 6), viscous=True, reynolds=50.0),
     "rotated_euler": lambda: rotated(warped((28, 24, 20)), (2, 2, 1), {1: (3, 1, 2), 2: (-1, -2, 3), 3: (1, -3, 2)}),
@@ -211,7 +214,8 @@ def test_free_stream_residual_gpu():
 @pytest.mark.parametrize("name,steps", [("vortex32", 10), ("ragged_euler", 4), ("tgv24", 5), ("split_ns", 3),
                                         ("ogrid_s4", 5), ("shock_warped", 20), ("rotated_euler", 4),
                                         ("rotated_ns", 3), ("tiny_ns3", 4), ("min6", 4), ("channel_ns", 5),
-                                        ("duct_euler", 10), ("duct_ns", 5), ("shock_vortex", 30)])
+                                        ("duct_euler", 10), ("duct_ns", 5), ("shock_vortex", 30),
+                                        ("long_xi_ns", 3), ("long_zeta_euler", 3)])
 def test_steps_parity(name, steps):
     w, ctx, P = pair(name)
     dt, _ = P.dt(0.5)
@@ -418,7 +422,7 @@ def test_mixed_precision_rhs_close():
     assert rel_linf(ctx.rhs(0), P.get_rhs(0), "rhs") < 1e-4
 
 
-@pytest.mark.parametrize("name", ["tgv24", "ragged_ns", "split_ns", "rotated_ns", "ogrid_s8"])
+@pytest.mark.parametrize("name", ["tgv24", "ragged_ns", "split_ns", "rotated_ns", "ogrid_s8", "long_xi_ns"])
 def test_mixed_precision_ns_rhs_close(name):
     """Mixed-form Navier-Stokes residual (FP32 node stress, viscous and
     inviscid fluxes) against the FP64 oracle on ragged blocks (partial
