@@ -19,8 +19,8 @@ cudaError_t flux_run_f32_d1(int, bool, const FluxArgs&, cudaStream_t);
 cudaError_t flux_run_f32_d2(int, bool, const FluxArgs&, cudaStream_t);
 
 FluxShape flux_shape(int dir, int v) {
-    if (dir == 0) return v == 0 ? FluxShape{32, 8} : v == 1 ? FluxShape{16, 16} : FluxShape{16, 8};
-    return v == 0 ? FluxShape{8, 32} : v == 1 ? FluxShape{16, 16} : FluxShape{8, 16};
+    if (dir == 0) return v == 0 ? FluxShape{32, 8} : v == 1 ? FluxShape{8, 8} : FluxShape{16, 8};
+    return v == 0 ? FluxShape{8, 32} : v == 1 ? FluxShape{8, 8} : FluxShape{8, 16};
 }
 
 int flux_ctas_per_sm(bool fp64, int dir, int v, bool visc, bool rk, int scheme) {

@@ -12,10 +12,10 @@
 
 namespace hx {
 
-// Candidate (nodes per chunk, lines per CTA): xi (32,8) (16,16) (16,8);
-// eta and zeta (8,32) (16,16) (8,16).
-constexpr int flux_tp(int dir, int v) { return dir == 0 ? (v == 0 ? 32 : 16) : (v == 1 ? 16 : 8); }
-constexpr int flux_na(int dir, int v) { return dir == 0 ? (v == 0 ? 8 : v == 1 ? 16 : 8) : (v == 0 ? 32 : 16); }
+// Candidate (nodes per chunk, lines per CTA): xi (32,8) (8,8) (16,8);
+// eta and zeta (8,32) (8,8) (8,16).
+constexpr int flux_tp(int dir, int v) { return dir == 0 ? (v == 0 ? 32 : v == 1 ? 8 : 16) : 8; }
+constexpr int flux_na(int dir, int v) { return v == 1 ? 8 : dir == 0 ? 8 : (v == 0 ? 32 : 16); }
 
 namespace {
 

@@ -27,7 +27,7 @@ std::mutex g_mu;
 std::vector<void*> g_addr;
 std::vector<int> g_sms;
 
-constexpr int kNA = 16, kVariant = 1;   // flux variant 1: 16 nodes per chunk x 16 lines, every direction
+constexpr int kNA = 8, kVariant = 1;   // flux variant 1: 8 nodes per chunk x 8 lines, every direction
 
 long long rup(long long v, long long m) { return (v + m - 1) / m * m; }
 
