@@ -604,19 +604,27 @@ def main():
     torch.cuda.synchronize()
     eclocks = Clocks(local)
     eclocks.start()
+    phases = []   # per step: copy in, RK3 step, copy out (host clock)
     t0 = time.perf_counter()
     for _ in range(e_steps):
+        ta = time.perf_counter()
         for b in range(len(w.blocks)):
             ectx.set_state(b, hq[b].numpy())
+        tb = time.perf_counter()
         ectx.step(1, dt)
+        tc = time.perf_counter()
         for b in range(len(w.blocks)):
             ectx.get_state(b, hout[b].numpy())
+        phases.append((tb - ta, tc - tb, time.perf_counter() - tc))
     e_secs = time.perf_counter() - t0
     eck = eclocks.stop()
     e_secs = max_over_ranks(e_secs)
     ectx.close()
     e2e = {"value": ranks.throughput(w.npts, e_steps, e_secs), "unit": "Mpts/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": h2d, "steps": e_steps, "clocks": eck}
+           "d2h_bytes_per_step": h2d, "steps": e_steps, "clocks": eck,
+           "median_ms": {k: statistics.median(ph[i] for ph in phases) * 1e3
+                         for i, k in enumerate(("copy_in", "step", "copy_out"))},
+           "max_ms": {k: max(ph[i] for ph in phases) * 1e3 for i, k in enumerate(("copy_in", "step", "copy_out"))}}
 
     if rank != 0:
         return
