@@ -15,9 +15,8 @@
 // Shared memory: each field plane is [slot][line]; a pair (lines 2a, 2a+1)
 // is one 8-byte word.  Along eta and zeta the lanes of a warp run across
 // the pairs (consecutive i: 64-bit global accesses); along xi they run along
-// the ring (consecutive i again), and the row of a slot is padded to an odd
-// number of pairs so that a half-warp's 64-bit accesses fall on distinct
-// banks.
+// the ring (consecutive i again), and the pair index is swizzled by the row
+// so that a half-warp's 64-bit accesses fall on distinct banks.
 #pragma once
 #include "hx_pair.cuh"
 
@@ -27,13 +26,20 @@ template <int DIR, int TP, int NP>
 struct Flux2Layout {
     static constexpr int NA = 2 * NP;                     // lines per CTA
     static constexpr int RING = TP >= 8 ? 2 * TP : 16;    // >= TP + 8 live nodes, power of two
-    static constexpr int RS = DIR == 0 ? NP + 1 : NP;     // pairs per ring row
+    static constexpr int RS = NP;                         // pairs per ring row
     static constexpr int PL = RING * RS * 2;              // floats per field plane
     // fields per ring slot: Q 5, metric 3, node flux 5, U^L (then h) 5, U^R 5, viscous node flux 4
     static constexpr int NF_INV = 23, NF_VISC = 27;
     static_assert((NP & (NP - 1)) == 0 && (TP & (TP - 1)) == 0, "power-of-two chunk and pair count");
-    // float offset of (node p >= -4 RING, pair a2) within a plane
-    __device__ static __forceinline__ int idx(int p, int a2) { return (((p + 4 * RING) & (RING - 1)) * RS + a2) * 2; }
+    // float offset of (node p >= -4 RING, pair a2) within a plane.  Along xi
+    // a half-warp reads 16 consecutive rows of one pair: the pair index is
+    // XORed with the row's bits above the 16 / NP rows that share a bank
+    // group, so that the 16 accesses fall on distinct banks.
+    __device__ static __forceinline__ int idx(int p, int a2) {
+        const int row = (p + 4 * RING) & (RING - 1);
+        if (DIR == 0) return (row * RS + (a2 ^ ((row / (16 / NP)) & (NP - 1)))) * 2;
+        return (row * RS + a2) * 2;
+    }
     // item it (>= 0) of a step over X nodes of NP pairs -> (node, pair)
     __device__ static __forceinline__ void split(int it, int X, int& p, int& a2) {
         const unsigned u = (unsigned)it;
