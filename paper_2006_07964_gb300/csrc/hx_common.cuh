@@ -777,12 +777,14 @@ __device__ __forceinline__ void face_flux(const GasR<R>& gs, const R ql[5], cons
 
 // Stress tensor and work + heat-flux vector at a node, Eqs. (5)-(6) and the
 // definitions under Eq. (1): S = (tau_xx, tau_yy, tau_zz, tau_xy, tau_xz,
-// tau_yz, beta_x, beta_y, beta_z) from g = (u,v,w,T)_(x,y,z), row-major.  The
+// tau_yz, beta_x, beta_y, beta_z) from g = (u,v,w,T)_(x,y,z) / sc, row-major
+// (S is linear in the gradients, so a common factor sc of all twelve, the
+// Jacobian of the chain rule, enters through the viscosity once).  The
 // viscous flux of a direction with metric m is then (m.tau_x., m.tau_y.,
 // m.tau_z., m.beta): the direction-independent part is formed once per node.
 template <class R>
-__device__ __forceinline__ void stress(const GasR<R>& gs, R u, R v, R w, R T, const R g[12], R S[9]) {
-    const R kv = gs.mach_re * viscosity(gs, T);
+__device__ __forceinline__ void stress(const GasR<R>& gs, R u, R v, R w, R T, const R g[12], R sc, R S[9]) {
+    const R kv = gs.mach_re * viscosity(gs, T) * sc;
     const R kq = kv * gs.kq_fac;
     const R div = g[0] + g[4] + g[8];
     const R lam = R(-2.0 / 3.0) * kv * div;

@@ -458,6 +458,11 @@ k_grad(const Brick* __restrict__ cols, int nb, const DevBlock* __restrict__ bloc
             hy_ = r < 3 ? r - 3 : br.nj + r - 3;
         }
         const long long hoff = hx_ + (long long)hy_ * B.sj - (long long)ti - (long long)tj * B.sj;
+        // whether this column lies within G of a joined i or j face, and
+        // whether the block has joined k faces: only such nodes push halo
+        const bool near_ij = (B.nbr[0] >= 0 && i < G) || (B.nbr[1] >= 0 && i >= B.n[0] - G) ||
+                             (B.nbr[2] >= 0 && j < G) || (B.nbr[3] >= 0 && j >= B.n[1] - G);
+        const bool nbrk = B.nbr[4] >= 0 || B.nbr[5] >= 0;
         // loads of plane k issued one plane ahead (own column at k + 3, the
         // halo node and the metrics at k), so that they arrive while plane
         // k - 1 is computed
@@ -525,22 +530,25 @@ k_grad(const Brick* __restrict__ cols, int nb, const DevBlock* __restrict__ bloc
                 dc[v][2] = dline<R>(fk, k, B.n[2], lo[2], hi[2]);
             }
             const R J = m[9];
-            R g[12];
+            R g[12];   // the gradients / J
 #pragma unroll
             for (int v = 0; v < 4; ++v)
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    g[v * 3 + c] = J * (m[c] * dc[v][0] + m[3 + c] * dc[v][1] + m[6 + c] * dc[v][2]);
+                    g[v * 3 + c] = m[c] * dc[v][0] + m[3 + c] * dc[v][1] + m[6 + c] * dc[v][2];
             if (STRESS) {
                 R S[9];
-                stress(gs, qv[3][0], qv[3][1], qv[3][2], qv[3][3], g, S);
+                stress(gs, qv[3][0], qv[3][1], qv[3][2], qv[3][3], g, J, S);
 #pragma unroll
                 for (int c = 0; c < 9; ++c) out[c * fs + e] = S[c];
-                const int id[3] = {i, j, k};
-                push_ghosts<R>(blocks, B, br.b, id, out, fs, 9, S, false);   // the stress halo of the sweeps
+                // the stress halo of the sweeps, from nodes within G of a joined face
+                if (near_ij || (nbrk && (k < G || k >= B.n[2] - G))) {
+                    const int id[3] = {i, j, k};
+                    push_ghosts<R>(blocks, B, br.b, id, out, fs, 9, S, false);
+                }
             } else {
 #pragma unroll
-                for (int c = 0; c < 12; ++c) out[c * fs + e] = g[c];
+                for (int c = 0; c < 12; ++c) out[c * fs + e] = J * g[c];
             }
         }
     }
