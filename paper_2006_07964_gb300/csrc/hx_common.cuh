@@ -286,8 +286,9 @@ __device__ __forceinline__ R mid6(R fm2, R fm1, R f0, R fp1, R fp2, R fp3) {
 }
 
 // Primitives (u, v, w, T) of a conservative state (T = gamma p / rho); the
-// one formula every kernel uses, so that results do not depend on which
-// kernel formed them.
+// one formula every kernel of the mixed form uses, so that results do not
+// depend on which kernel formed them.  The FP64 form forms them only in
+// k_prep, from the node state (node_state below).
 template <class R>
 __device__ __forceinline__ void primitives(const GasR<R>& gs, const R q[5], R pv[4]) {
     const R irho = hrcp(q[0]);
@@ -528,35 +529,87 @@ __device__ __forceinline__ void weno_face10(const float (&W)[6][5], float (&WL)[
 //   U_4 = |u|^2/2 Wk + rho u.C + al (s H + c theta t),  al = rho/(sqrt(2) c),
 // which is the matrix pair L = T_k^-1, R = T_k entry by entry.
 // ---------------------------------------------------------------------------
+// The direction-independent part of a node's basis: 1/rho, the velocity,
+// |u|^2/2, p, c, a0 = 1 - phi2/c^2, g = (gamma-1)/c^2, c/(sqrt(2) rho),
+// rho/(sqrt(2) c) and H.  The FP64 form forms it once per node and stage
+// (k_prep, NodeState::NF fields of a node-state array) and its three sweeps
+// read it, instead of each sweep dividing and taking the square root again.
+template <class R>
+struct NodeState {
+    static constexpr int NF = 12;
+    R irho, u, v, w, half_uu, p, c, a0, g, cir, al, H;
+};
+
+// Returns c^2 = gamma p / rho, the temperature of the primitives.
+template <class R>
+__device__ __forceinline__ R node_state(const GasR<R>& gs, const R q[5], NodeState<R>& s) {
+    const R rho = q[0];
+    s.irho = hrcp(rho);
+    s.u = q[1] * s.irho;
+    s.v = q[2] * s.irho;
+    s.w = q[3] * s.irho;
+    s.half_uu = R(0.5) * (s.u * s.u + s.v * s.v + s.w * s.w);
+    s.p = gs.gm1 * (q[4] - rho * s.half_uu);
+    const R c2 = gs.gamma * s.p * s.irho;
+    const R ic = hrsqrt(c2);
+    s.c = c2 * ic;
+    const R phi2 = gs.gm1 * s.half_uu;
+    const R ic2 = ic * ic;
+    s.a0 = R(1) - phi2 * ic2;
+    s.g = gs.gm1 * ic2;
+    s.cir = s.c * s.irho * R(0.70710678118654752440);
+    s.al = rho * ic * R(0.70710678118654752440);
+    s.H = s.half_uu + c2 * gs.inv_gm1;
+    return c2;
+}
+
 // FP64: per-node products are hoisted out of the five stencil projections
 // (the FP64 pipe is the bound; registers are not).
 template <class R>
 struct CharBasis {
     R kx, ky, kz, u, v, w, rho, irho, p, c, a0, g, gu, gv, gw, cir, kxi, kyi, kzi, kxs, kys, kzs, al, alc, acth,
         half_uu, H;
-    // the state part (the node flux needs only this) ...
-    __device__ __forceinline__ void init_state(const GasR<R>& gs, const R q[5]) {
-        irho = hrcp(q[0]);
-        rho = q[0];
-        u = q[1] * irho;
-        v = q[2] * irho;
-        w = q[3] * irho;
-        half_uu = R(0.5) * (u * u + v * v + w * w);
-        p = gs.gm1 * (q[4] - rho * half_uu);
-        const R c2 = gs.gamma * p * irho;
-        const R ic = hrsqrt(c2);
-        c = c2 * ic;
-        const R phi2 = gs.gm1 * half_uu;
-        const R ic2 = ic * ic;
-        a0 = R(1) - phi2 * ic2;
-        g = gs.gm1 * ic2;
+    __device__ __forceinline__ void set_state(R rho_, const NodeState<R>& s) {
+        rho = rho_;
+        irho = s.irho;
+        u = s.u;
+        v = s.v;
+        w = s.w;
+        half_uu = s.half_uu;
+        p = s.p;
+        c = s.c;
+        a0 = s.a0;
+        g = s.g;
+        cir = s.cir;
+        al = s.al;
+        H = s.H;
         gu = g * u;
         gv = g * v;
         gw = g * w;
-        cir = c * irho * R(0.70710678118654752440);
-        al = rho * ic * R(0.70710678118654752440);
         alc = al * c;
-        H = half_uu + c2 * gs.inv_gm1;
+    }
+    // the state part (the node flux needs only this) ...
+    __device__ __forceinline__ void init_state(const GasR<R>& gs, const R q[5]) {
+        NodeState<R> s;
+        node_state(gs, q, s);
+        set_state(q[0], s);
+    }
+    // ... or read from a node-state array (field stride fs) at the node
+    __device__ __forceinline__ void load_state(const R* __restrict__ ns, long long fs, R rho_) {
+        NodeState<R> s;
+        s.irho = ns[0];
+        s.u = ns[fs];
+        s.v = ns[2 * fs];
+        s.w = ns[3 * fs];
+        s.half_uu = ns[4 * fs];
+        s.p = ns[5 * fs];
+        s.c = ns[6 * fs];
+        s.a0 = ns[7 * fs];
+        s.g = ns[8 * fs];
+        s.cir = ns[9 * fs];
+        s.al = ns[10 * fs];
+        s.H = ns[11 * fs];
+        set_state(rho_, s);
     }
     // ... and the unit normal k.  The projection works on rho d = (Q_m - u_m
     // Q_0); 1/rho and 1/sqrt(2) go into the normal once per node.

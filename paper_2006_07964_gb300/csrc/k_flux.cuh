@@ -5,8 +5,8 @@
 // over a list of line groups) and marches along them in chunks of TP nodes,
 // keeping a ring of RING nodes per line in shared memory.  Every node's
 // work is done once; per chunk c (nodes c*TP ..):
-//   load  state and metric of d at nodes c*TP+3 .. c*TP+TP+2 (FP64: and the
-//         stored unit normals); FP32: L2 prefetch hints for this chunk's
+//   load  state and metric of d at nodes c*TP+3 .. c*TP+TP+2 (FP64: the
+//         state only); FP32: L2 prefetch hints for this chunk's
 //         output step and the next chunk's load and node steps;
 //   node  at nodes c*TP+1 .. c*TP+TP: characteristic projection of the
 //         5-node stencil at the node (modified AFWENO, Sec. 4.5.1,
@@ -14,6 +14,7 @@
 //         value at its - face (Eqs. (13)-(17)), back projection; the node
 //         flux (Eq. (4)) and, for Navier-Stokes, the node viscous flux of d
 //         from the node's stress tensor and heat flux (Eqs. (5)-(6));
+//         FP64 reads the node's basis state (k_prep) and unit normal;
 //   face  at faces c*TP .. c*TP+TP-1: sixth-order midpoint metric and the
 //         Steger-Warming numerical flux h = F+(U^L) + F-(U^R) (Eq. (12));
 //   out   at nodes c*TP-2 .. c*TP+TP-3 (two behind, so that every input is
@@ -81,8 +82,9 @@ struct FluxLayout {
 // SCH 0: modified AFWENO (characteristic space at the node, Figs. 10-11);
 // SCH 1: original AFWENO (characteristic space at the face from the mean
 // state and the face metric, two independent WENOs per face, Fig. 9).
-// NRM (FP64 with the stored unit normals of k_normals): the node basis and
-// the face metric are read from them instead of formed from the metric.
+// NRM (FP64 with the stored unit normals of k_normals and the node state of
+// k_prep): the node basis and the face metric are read from them instead of
+// formed from the metric and the state.
 // Resident CTAs per SM that the register allocation must allow.  FP64: two
 // of 256 threads (128 registers) or three of 128, so that the FP64 pipe
 // always has a second CTA's warps (four of 128 spill at 128 registers and
@@ -100,8 +102,9 @@ constexpr int flux_min_ctas() {
 template <class R, int DIR, int TP, int NA, bool VISC, bool RK, int SCH, bool NRM>
 __global__ void __launch_bounds__(TP * NA, flux_min_ctas<R, TP * NA, VISC, NRM>())
 k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int ntiles,
-       const R* __restrict__ Q, const R* __restrict__ met, const R* __restrict__ nrm, long long fs,
-       const R* __restrict__ stress, R* __restrict__ A, int accumulate, GasR<R> gs, RKArgs rk) {
+       const R* __restrict__ Q, const R* __restrict__ met, const R* __restrict__ nrm,
+       const R* __restrict__ nst, long long fs, const R* __restrict__ stress, R* __restrict__ A, int accumulate,
+       GasR<R> gs, RKArgs rk) {
     using LY = FluxLayout<DIR, TP, NA>;
     constexpr int PL = LY::PLANE;
     constexpr int NT = TP * NA;
@@ -215,8 +218,8 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         mz = sM[2 * PL + s0];
                     }
                     CharBasis<R> cb;
-                    if (NRM)
-                        cb.init_state(gs, q);
+                    if constexpr (NRM)
+                        cb.load_state(nst + e, fs, q[0]);
                     else
                         cb.init(gs, q, mx, my, mz);
                     // node flux along the un-normalised metric, Eq. (4)

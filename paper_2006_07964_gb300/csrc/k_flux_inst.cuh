@@ -23,8 +23,8 @@ namespace {
 // two-lines-per-thread kernel of k_flux2.cuh (TP x NA/2 threads); the FP64
 // form and the original scheme run k_flux.  Only the FP64 form fuses the RK
 // stage into its zeta sweep.  FP64 contexts read the sweeps' stored unit
-// normals (NRM); a call without them (the allocation-free Euler residual)
-// runs the FP64 Euler sweep that forms them from the metric.
+// normals and the node state of k_prep (NRM); a call without them (the
+// allocation-free Euler residual) runs the FP64 Euler sweep that forms both.
 template <class R, int DIR, int V, bool VISC, bool RK = false, int SCH = 0>
 struct FluxInst {
     static constexpr int TP = flux_tp(DIR, V), NA = flux_na(DIR, V);
@@ -72,20 +72,21 @@ struct FluxInst {
                 (float*)a.A, a.accumulate, gs);
         } else if constexpr (F64) {
             if (a.nrm) {
+                if (!a.nst) return cudaErrorInvalidValue;   // the node state comes with the normals
                 k_flux<R, DIR, TP, NA, VISC, RK, SCH, true><<<a.grid, NT, smem, s>>>(
-                    a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, (const R*)a.nrm, a.fs,
-                    (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
+                    a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, (const R*)a.nrm, (const R*)a.nst,
+                    a.fs, (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
             } else if constexpr (PLAIN64) {
                 k_flux<R, DIR, TP, NA, VISC, RK, SCH, false><<<a.grid, NT, smem_plain, s>>>(
-                    a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, nullptr, a.fs, (const R*)a.stress,
-                    (R*)a.A, a.accumulate, gs, a.rk);
+                    a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, nullptr, nullptr, a.fs,
+                    (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
             } else {
                 return cudaErrorInvalidValue;   // FP64 sweeps other than the Euler one need the stored normals
             }
         } else {
             k_flux<R, DIR, TP, NA, VISC, RK, SCH, false><<<a.grid, NT, smem, s>>>(
-                a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, nullptr, a.fs, (const R*)a.stress,
-                (R*)a.A, a.accumulate, gs, a.rk);
+                a.blocks, a.tiles, a.ntiles, (const R*)a.Q, (const R*)a.met, nullptr, nullptr, a.fs,
+                (const R*)a.stress, (R*)a.A, a.accumulate, gs, a.rk);
         }
         return cudaGetLastError();
     }

@@ -18,6 +18,7 @@ struct FluxArgs {
     const void* stress; // R, 9 fields (tau_xx, tau_yy, tau_zz, tau_xy, tau_xz, tau_yz, beta), Navier-Stokes only
     void* A;            // R, 5 fields, accumulated divergence
     const void* nrm;    // FP64 form: the sweep normals (k_normals, 21 fields), or null
+    const void* nst;    // FP64 form with nrm: the node state (k_prep, NodeState<double>::NF fields)
     int accumulate;
     Gas gas;
     int grid;           // CTAs of the persistent launch
@@ -70,10 +71,11 @@ cudaError_t launch_rk_stage(const Brick* bricks, int nb, const DevBlock* blocks,
 // Far-field boundary nodes after a stage.
 cudaError_t launch_bc_farfield(const NodeItem* items, int n, const DevBlock* blocks, double* Q, float* Qf,
                                float* primf, const double* met, long long fs, Gas gas, cudaStream_t s);
-// Ghosts of the stencil state and (prim != null) primitives over the bricks
-// of the interior and the ghost slabs.
+// Ghosts of the stencil state, (prim != null) primitives and (FP64, nst !=
+// null) the node state of the sweeps over the bricks of the interior and the
+// ghost slabs.
 cudaError_t launch_prep(const Brick* bricks, int nb, const DevBlock* blocks, void* Q, bool fp64, long long fs,
-                        const void* met, void* prim, Gas gas, cudaStream_t s);
+                        const void* met, void* prim, double* nst, Gas gas, cudaStream_t s);
 cudaError_t launch_dt(const Brick* bricks, int nb, const DevBlock* blocks, const double* Q, const double* met,
                       long long fs, Gas gas, unsigned long long* bmax, cudaStream_t s);
 cudaError_t launch_rhs_out(DevBlock B, const void* A, const float* Aref, bool fp64, const double* met, long long fs,

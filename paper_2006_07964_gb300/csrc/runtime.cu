@@ -66,6 +66,7 @@ struct hx_ctx {
 
     double *met = nullptr, *Qn = nullptr, *Qa = nullptr, *Qb = nullptr, *stage = nullptr;
     double* nrm = nullptr;     // FP64 form: unit normals of the sweeps (k_normals), 21 fields
+    double* nst = nullptr;     // FP64 form: node state of the sweeps (k_prep), NodeState<double>::NF fields
     float *metf = nullptr;
     float* Aref = nullptr;   // mixed form: FP32 divergence of the rest state (pure rounding)
     float* Qf[3] = {nullptr, nullptr, nullptr};   // mixed form: FP32 copies of Qn, Qa, Qb
@@ -298,12 +299,19 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
     }
     if (prep) {
         if (pf) pf->begin(K_PREP);
+        // the FP64 form's node state covers the interior and the ghosts
+        double* nst = f64 ? ctx->nst : nullptr;
         if (visc && prim_interior)
-            HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, ctx->gas, s));
+            HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, nst, ctx->gas,
+                              s));
         else if (visc)
-            HX_CK(launch_prep(ctx->d_ghost, ctx->n_ghost, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, ctx->gas, s));
+            HX_CK(launch_prep(ctx->d_ghost, ctx->n_ghost, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, nullptr,
+                              ctx->gas, s));
+        else if (nst)
+            HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, nullptr, nst, ctx->gas, s));
         else
-            HX_CK(launch_prep(ctx->d_ghost, ctx->n_ghost, ctx->d_blocks, Qs, f64, ctx->fs, M, nullptr, ctx->gas, s));
+            HX_CK(launch_prep(ctx->d_ghost, ctx->n_ghost, ctx->d_blocks, Qs, f64, ctx->fs, M, nullptr, nullptr,
+                              ctx->gas, s));
         if (pf) pf->end();
     }
     if (visc) {
@@ -321,6 +329,7 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
         a.Q = Qs;
         a.met = M;
         a.nrm = ctx->nrm;
+        a.nst = ctx->nst;
         a.fs = ctx->fs;
         a.stress = ctx->grad;
         a.A = ctx->A;
@@ -416,6 +425,9 @@ int autotune(hx_ctx* ctx) {
     }
     long long cls = 1;
     while (cls < tot) cls <<= 1;
+    if (f64 && ctx->cfg.autotune)   // the node state of the state the FP64 sweeps are timed on
+        HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, stencil_state(ctx, 0), true, ctx->fs,
+                          stencil_met(ctx), visc ? ctx->prim : nullptr, ctx->nst, ctx->gas, ctx->stream));
     for (int d = 0; d < 3; ++d) {
         auto key = std::make_tuple((int)f64 + 2 * ctx->cfg.scheme, d, (int)visc, cls, nmin[d], (int)ctx->blocks.size());
         {
@@ -447,6 +459,7 @@ int autotune(hx_ctx* ctx) {
                 a.Q = stencil_state(ctx, 0);
                 a.met = stencil_met(ctx);
                 a.nrm = ctx->nrm;
+                a.nst = ctx->nst;
                 a.fs = ctx->fs;
                 a.stress = ctx->grad;
                 a.A = ctx->A;
@@ -846,6 +859,8 @@ int hx_finalize(hx_ctx* ctx) {
     if (ctx->fp64()) {
         if ((rc = dalloc(ctx, (void**)&ctx->nrm, 21 * fs * 8))) return rc;
         HX_CK(launch_fill(ctx->nrm, true, 21 * ctx->fs, 0.0, ctx->stream));
+        if ((rc = dalloc(ctx, (void**)&ctx->nst, NodeState<double>::NF * fs * 8))) return rc;
+        HX_CK(launch_fill(ctx->nst, true, NodeState<double>::NF * ctx->fs, 1.0, ctx->stream));
     } else {
         for (int q = 0; q < 3; ++q)
             if ((rc = dalloc(ctx, (void**)&ctx->Qf[q], 5 * fs * 4))) return rc;
@@ -1085,7 +1100,8 @@ int hx_get_gradients(hx_ctx* ctx, int block, double* g_out, int on_device) {
     const bool f64 = ctx->fp64();
     void* Qs = stencil_state(ctx, 0);
     const void* M = stencil_met(ctx);
-    HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, ctx->gas, ctx->stream));
+    HX_CK(launch_prep(ctx->d_prep, ctx->n_prep, ctx->d_blocks, Qs, f64, ctx->fs, M, ctx->prim, f64 ? ctx->nst : nullptr,
+                      ctx->gas, ctx->stream));
     HX_CK(launch_grad(ctx->d_col, ctx->n_col, ctx->d_blocks, ctx->prim, M, f64, ctx->fs, ctx->grad, false, ctx->gas,
                       ctx->stream));
     return get_field(ctx, block, ctx->grad, f64, 12, g_out, on_device);
