@@ -334,9 +334,10 @@ struct WenoParts {   // one field: value = u2 + n / (8 d) for each side
     double nL, nR, dL, dR, uL2, uR2;
 };
 
-__device__ __forceinline__ WenoParts weno_parts(double w0, double w1, double w2, double w3, double w4) {
+// From the first differences d10 .. d43 of the stencil values and the
+// central value w2 (the only places the values enter).
+__device__ __forceinline__ WenoParts weno_parts_d(double d10, double d21, double d32, double d43, double w2) {
     const double eps4 = 4.0e-6;
-    const double d10 = w1 - w0, d21 = w2 - w1, d32 = w3 - w2, d43 = w4 - w3;
     const double a1 = d21 - d10, a2 = d32 - d21, a3 = d43 - d32;
     const double c1 = fma(2.0, d21, a1), c2 = d21 + d32, c3 = fma(-2.0, d32, a3);
     const double k = 13.0 / 3.0;
@@ -357,6 +358,10 @@ __device__ __forceinline__ WenoParts weno_parts(double w0, double w1, double w2,
     r.uL2 = fma(0.125, fma(3.0, d32, d21), w2);    // (-w1 + 6 w2 + 3 w3) / 8
     r.uR2 = fma(-0.125, fma(3.0, d21, d32), w2);   // (-w3 + 6 w2 + 3 w1) / 8
     return r;
+}
+
+__device__ __forceinline__ WenoParts weno_parts(double w0, double w1, double w2, double w3, double w4) {
+    return weno_parts_d(w1 - w0, w2 - w1, w3 - w2, w4 - w3, w2);
 }
 
 __device__ __forceinline__ void weno_pair(double w0, double w1, double w2, double w3, double w4,
@@ -395,14 +400,19 @@ __device__ __forceinline__ void batch_recip(const double (&D)[N], double num, do
         inv[l] = __longlong_as_double(__double_as_longlong(inv[l]) - ((long long)(ex[l] - 1023) << 52));
 }
 
-// The five characteristic fields of a node with one FP64 division.
-// W[s][l]: stencil node s = 0..4 (i-2..i+2), field l.
-__device__ __forceinline__ void weno_pair5(const double (&W)[5][5], double (&WL)[5], double (&WR)[5]) {
+// The five characteristic fields of a node with one FP64 division, from
+// the differences dW[s][l] of the stencil's characteristic values across
+// its faces s = 0..3 (i-3/2 .. i+3/2) and the node's own values Wc[l].
+// The projection is linear, so dW is the projection of the differences of
+// the conservative state: formed once per face, shared by the four
+// stencils that contain the face.
+__device__ __forceinline__ void weno_pair5_d(const double (&dW)[4][5], const double (&Wc)[5], double (&WL)[5],
+                                             double (&WR)[5]) {
     WenoParts r[5];
     double D[5], inv[5];
 #pragma unroll
     for (int l = 0; l < 5; ++l) {
-        r[l] = weno_parts(W[0][l], W[1][l], W[2][l], W[3][l], W[4][l]);
+        r[l] = weno_parts_d(dW[0][l], dW[1][l], dW[2][l], dW[3][l], Wc[l]);
         D[l] = r[l].dL * r[l].dR;
     }
     batch_recip<5>(D, 0.125, inv);

@@ -6,11 +6,14 @@
 // keeping a ring of RING nodes per line in shared memory.  Every node's
 // work is done once; per chunk c (nodes c*TP ..):
 //   load  state and metric of d at nodes c*TP+3 .. c*TP+TP+2 (FP64: the
-//         state only); FP32: L2 prefetch hints for this chunk's
-//         output step and the next chunk's load and node steps;
+//         state only) and, for the modified scheme, the state difference
+//         across the face before each; FP32: L2 prefetch hints for this
+//         chunk's output step and the next chunk's load and node steps;
 //   node  at nodes c*TP+1 .. c*TP+TP: characteristic projection of the
 //         5-node stencil at the node (modified AFWENO, Sec. 4.5.1,
-//         Figs. 10-11), WENO5 left value at the node's + face and right
+//         Figs. 10-11; the projection is linear, so the WENO's first
+//         differences are the projected state differences of the stencil's
+//         four faces), WENO5 left value at the node's + face and right
 //         value at its - face (Eqs. (13)-(17)), back projection; the node
 //         flux (Eq. (4)) and, for Navier-Stokes, the node viscous flux of d
 //         from the node's stress tensor and heat flux (Eqs. (5)-(6));
@@ -39,7 +42,8 @@ struct FluxLayout {
     static constexpr int PLANE = RING * NA;
     // fields per ring slot: Q 5, metric 3, node flux 5, U^L (then h) 5, U^R 5, viscous node flux 4;
     // with stored normals (NRM) the metric and the normals are read at the
-    // node and face that use them, not staged: 3 fields fewer
+    // node and face that use them, not staged: 3 fields fewer; the modified
+    // scheme (DQ) adds the state difference Q_(p+1) - Q_p across face p+1/2: 5
     static constexpr int NF_INV = 23, NF_VISC = 27;
     static_assert((NA & (NA - 1)) == 0 && (TP & (TP - 1)) == 0 && (RING & (RING - 1)) == 0,
                   "power-of-two line count, chunk and ring");
@@ -69,9 +73,9 @@ struct FluxLayout {
             p = (int)(u / NA);
         }
     }
-    template <class R, bool VISC, bool NRM>
+    template <class R, bool VISC, bool NRM, bool DQ>
     static constexpr size_t smem_bytes() {
-        return sizeof(R) * (size_t)PLANE * ((VISC ? NF_VISC : NF_INV) - (NRM ? 3 : 0));
+        return sizeof(R) * (size_t)PLANE * ((VISC ? NF_VISC : NF_INV) - (NRM ? 3 : 0) + (DQ ? 5 : 0));
     }
 };
 
@@ -116,6 +120,7 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
     R* sUL = sF + 5 * PL;                      // 5 (U^L at the + face, then h)
     R* sUR = sUL + 5 * PL;                     // 5 (U^R at the - face)
     R* sFv = sUR + 5 * PL;                     // 4 (VISC)
+    R* sD = sFv + (VISC ? 4 : 0) * PL;         // 5 (SCH 0): Q_(p+1) - Q_p at slot p
     const int tid = threadIdx.x;
 
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -141,8 +146,18 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                     if (a0 + a >= na || p > n + 2) continue;
                     const long long e = hx_chk(B, e0 + p * sd + a * sa);
                     const int s = LY::idx(p, a);
+                    R qp[5];
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) sQ[f * PL + s] = Q[f * fs + e];
+                    for (int f = 0; f < 5; ++f) {
+                        qp[f] = Q[f * fs + e];
+                        sQ[f * PL + s] = qp[f];
+                    }
+                    if (SCH == 0 && p > -3) {   // the face p-1/2 (its left node from global memory)
+                        const long long em = hx_chk(B, e - sd);
+                        const int sl = LY::idx(p - 1, a);
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) sD[f * PL + sl] = qp[f] - Q[f * fs + em];
+                    }
                     if (!NRM) {
 #pragma unroll
                         for (int f = 0; f < 3; ++f) sM[f * PL + s] = met[(3 * DIR + f) * fs + e];
@@ -246,29 +261,30 @@ k_flux(const DevBlock* __restrict__ blocks, const Tile* __restrict__ tiles, int 
                         if (LATE_FV) put_fv();
                         continue;
                     }
-                    if (NRM) {   // node normal (defined on nodes -1 .. n)
-                        const R* nr = nrm + 7 * DIR * fs + e;
-                        cb.set_normal(nr[0], nr[fs], nr[2 * fs]);
-                    }
-                    R W[5][5];
-#pragma unroll
-                    for (int s = -2; s <= 2; ++s) {
-                        if (s == 0) {   // the node's own state: closed form
-                            cb.center(gs, W[2]);
-                            continue;
+                    if constexpr (SCH == 0) {
+                        if (NRM) {   // node normal (defined on nodes -1 .. n)
+                            const R* nr = nrm + 7 * DIR * fs + e;
+                            cb.set_normal(nr[0], nr[fs], nr[2 * fs]);
                         }
-                        const int si = LY::idx(p + s, a);
-                        cb.project(sQ[si], sQ[PL + si], sQ[2 * PL + si], sQ[3 * PL + si], sQ[4 * PL + si], W[s + 2]);
+                        // the stencil's characteristic differences across faces
+                        // p-3/2 .. p+3/2, and the node's own values in closed form
+                        R dW[4][5], Wc[5];
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) {
+                            const int si = LY::idx(p - 2 + s, a);
+                            cb.project(sD[si], sD[PL + si], sD[2 * PL + si], sD[3 * PL + si], sD[4 * PL + si], dW[s]);
+                        }
+                        cb.center(gs, Wc);
+                        R WL[5], WR[5];
+                        weno_pair5_d(dW, Wc, WL, WR);
+                        R U[5];
+                        cb.back(WL, U);
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) sUL[f * PL + s0] = U[f];
+                        cb.back(WR, U);
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) sUR[f * PL + s0] = U[f];
                     }
-                    R WL[5], WR[5];
-                    weno_pair5(W, WL, WR);
-                    R U[5];
-                    cb.back(WL, U);
-#pragma unroll
-                    for (int f = 0; f < 5; ++f) sUL[f * PL + s0] = U[f];
-                    cb.back(WR, U);
-#pragma unroll
-                    for (int f = 0; f < 5; ++f) sUR[f * PL + s0] = U[f];
                     if (LATE_FV) put_fv();
                 }
             }

@@ -34,8 +34,8 @@ struct FluxInst {
     static_assert(!RK || F64, "the fused RK stage is the FP64 form's");
     static constexpr int NT = PAIR ? TP * NA / 2 : TP * NA;
     static constexpr size_t smem = PAIR ? Flux2Layout<DIR, TP, NA / 2>::smem_bytes(VISC)
-                                        : FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC, F64>();
-    static constexpr size_t smem_plain = FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC, false>();
+                                        : FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC, F64, SCH == 0>();
+    static constexpr size_t smem_plain = FluxLayout<DIR, TP, NA>::template smem_bytes<R, VISC, false, SCH == 0>();
     static auto kernel() {
         if constexpr (PAIR)
             return k_flux2<DIR, TP, NA / 2, VISC>;
