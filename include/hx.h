@@ -91,9 +91,10 @@ typedef struct {
                              (16 x 8 along xi, 8 x 16 across), reproducible for
                              profiling                                               */
     int debug_poison;     /* 1 (checking only, slower): before every stage the ghost
-                             nodes of the stencil state, primitives, node stress and
-                             accumulator are set to NaN, so that a ghost the halo
-                             fill misses turns the result non-finite; 0: off        */
+                             nodes of the stencil state, primitives, node stress,
+                             accumulator and (FP64) the sweeps' node state are set
+                             to NaN, so that a ghost the halo fill misses turns the
+                             result non-finite; 0: off                              */
 } hx_config;
 
 typedef struct hx_ctx hx_ctx;

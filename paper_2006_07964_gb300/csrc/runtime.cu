@@ -296,6 +296,9 @@ int enqueue_rhs(hx_ctx* ctx, int in, const RKArgs* rk, Prof* pf, bool prep = tru
             HX_CK(launch_poison(ctx->d_shell, ctx->n_shell, ctx->d_blocks, ctx->prim, f64, ctx->fs, 4, s));
             HX_CK(launch_poison(ctx->d_shell, ctx->n_shell, ctx->d_blocks, ctx->grad, f64, ctx->fs, 12, s));
         }
+        if (f64)
+            HX_CK(launch_poison(ctx->d_shell, ctx->n_shell, ctx->d_blocks, ctx->nst, true, ctx->fs,
+                                NodeState<double>::NF, s));
     }
     if (prep) {
         if (pf) pf->begin(K_PREP);

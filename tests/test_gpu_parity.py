@@ -555,9 +555,10 @@ def test_local_time_stepping_mixed_close():
                                   "shock_warped"])
 def test_poisoned_ghosts_change_nothing(name, precision):
     """Halo completeness: with every ghost node of the stencil state,
-    primitives, node stress and accumulator set to NaN before each stage, the
-    residual and two steps are bitwise those of the normal run (a ghost the
-    halo fill misses, and a stencil reads, would turn them non-finite)."""
+    primitives, node stress, accumulator and (FP64) the sweeps' node state
+    set to NaN before each stage, the residual and two steps are bitwise
+    those of the normal run (a ghost the halo fill misses, and a stencil
+    reads, would turn them non-finite)."""
     w = CASES[name]()
     ref = hx.from_workload(w, precision=precision)
     chk = hx.from_workload(w, precision=precision, debug_poison=1)
