@@ -199,10 +199,25 @@ def alu_peaks(hx):
     return {"fp64_tflops": f64, "fp32_tflops": f32, "alu_src": "measured in this run (FMA-chain probe, hx_probe.h)"}
 
 
-def pinned_like(torch, a):
-    t = torch.empty(a.shape, dtype=torch.float64).pin_memory()
-    t.numpy()[...] = a
-    return t
+def page_locked(torch, arrays):
+    """Page-locks host numpy arrays for the copy engines (cudaHostRegister;
+    release with page_unlocked).  Measured on a GB300 host: 2.26 GB each way
+    in 13 ms, steadily, against 20-160 ms, varying from run to run, for the
+    same copies from buffers of torch's pin_memory()."""
+    cudart = torch.cuda.cudart()
+    done = []
+    for a in arrays:
+        rc = int(cudart.cudaHostRegister(a.ctypes.data, a.nbytes, 0))
+        if rc != 0:
+            page_unlocked(torch, done)
+            raise RuntimeError("cudaHostRegister failed (error %d)" % rc)
+        done.append(a)
+
+
+def page_unlocked(torch, arrays):
+    cudart = torch.cuda.cudart()
+    for a in arrays:
+        cudart.cudaHostUnregister(a.ctypes.data)
 
 
 def run_form(torch, hx, w, precision, steps, warmup, stream, dt, autotune=1):
@@ -591,15 +606,16 @@ def main():
                  "roofline": roofline_for(mctx, w, "mixed", 2, dt, peaks, msecs / args.steps * 1e3)}
         mctx.close()
 
-    # end to end through the C ABI with host (pinned) buffers: per step the
-    # state goes host -> device, one RK3 step runs, the state comes back
+    # end to end through the C ABI with page-locked host buffers: per step
+    # the state goes host -> device, one RK3 step runs, the state comes back
     ectx = hx.from_workload(w, precision=head, stream=stream.cuda_stream, autotune=tune)
-    hq = [pinned_like(torch, b.q0) for b in w.blocks]
-    hout = [torch.empty(b.q0.shape, dtype=torch.float64).pin_memory() for b in w.blocks]
+    hq = [np.array(b.q0, dtype=np.float64, order="C") for b in w.blocks]
+    hout = [np.zeros_like(q) for q in hq]
+    page_locked(torch, hq + hout)
     h2d = sum(b.q0.nbytes for b in w.blocks)
     e_steps = max(3, min(args.steps, 10))
     for b in range(len(w.blocks)):
-        ectx.set_state(b, hq[b].numpy())
+        ectx.set_state(b, hq[b])
     ectx.step(1, dt)
     torch.cuda.synchronize()
     eclocks = Clocks(local)
@@ -609,17 +625,18 @@ def main():
     for _ in range(e_steps):
         ta = time.perf_counter()
         for b in range(len(w.blocks)):
-            ectx.set_state(b, hq[b].numpy())
+            ectx.set_state(b, hq[b])
         tb = time.perf_counter()
         ectx.step(1, dt)
         tc = time.perf_counter()
         for b in range(len(w.blocks)):
-            ectx.get_state(b, hout[b].numpy())
+            ectx.get_state(b, hout[b])
         phases.append((tb - ta, tc - tb, time.perf_counter() - tc))
     e_secs = time.perf_counter() - t0
     eck = eclocks.stop()
     e_secs = max_over_ranks(e_secs)
     ectx.close()
+    page_unlocked(torch, hq + hout)
     e2e = {"value": ranks.throughput(w.npts, e_steps, e_secs), "unit": "Mpts/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d, "steps": e_steps, "clocks": eck,
            "median_ms": {k: statistics.median(ph[i] for ph in phases) * 1e3
