@@ -253,7 +253,7 @@ __device__ __forceinline__ float hmin0(float x) { return fminf(x, 0.0f); }
 
 template <class R>
 struct GasR {   // gas constants in the working precision (built on the host)
-    R gamma, gm1, inv_2gamma, two_gm1, mach_re, kq_fac, suth, one_p_suth, inv_gm1;
+    R gamma, gm1, inv_2gamma, two_gm1, mach_re, kq_fac, suth, one_p_suth, inv_gm1, g_gm1;
     R gm1_over_g, inv_g_sqrt2;   // (gamma-1)/gamma and 1/(gamma sqrt 2): a node's own characteristic values
     int mu_law;
     __host__ __device__ void init(const Gas& g) {
@@ -268,6 +268,7 @@ struct GasR {   // gas constants in the working precision (built on the host)
         suth = R(g.suth);
         one_p_suth = R(1.0 + g.suth);
         inv_gm1 = R(1.0 / (g.gamma - 1.0));
+        g_gm1 = R(g.gamma * (g.gamma - 1.0));
         mu_law = g.mu_law;
     }
 };
@@ -578,7 +579,7 @@ __device__ __forceinline__ R node_state(const GasR<R>& gs, const R q[5], NodeSta
 template <class R>
 struct CharBasis {
     R kx, ky, kz, u, v, w, rho, irho, p, c, a0, g, gu, gv, gw, cir, kxi, kyi, kzi, kxs, kys, kzs, al, alc, acth,
-        half_uu, H;
+        half_uu, H, rkx, rky, rkz;
     __device__ __forceinline__ void set_state(R rho_, const NodeState<R>& s) {
         rho = rho_;
         irho = s.irho;
@@ -634,6 +635,9 @@ struct CharBasis {
         kys = kyi * R(0.70710678118654752440);
         kzs = kzi * R(0.70710678118654752440);
         acth = alc * (kx * u + ky * v + kz * w);
+        rkx = rho * kx;
+        rky = rho * ky;
+        rkz = rho * kz;
     }
     __device__ __forceinline__ void init(const GasR<R>& gs, const R q[5], R mx, R my, R mz) {
         init_state(gs, q);
@@ -662,17 +666,17 @@ struct CharBasis {
         W[3] = base + kd;
         W[4] = base - kd;
     }
-    // U = R W
+    // U = R W, with rho C = (rho k) x (W_0, W_1, W_2) from the node's rho k
     __device__ __forceinline__ void back(const R W[5], R U[5]) const {
         const R Wk = kx * W[0] + ky * W[1] + kz * W[2];
-        const R Cx = ky * W[2] - kz * W[1], Cy = kz * W[0] - kx * W[2], Cz = kx * W[1] - ky * W[0];
+        const R rCx = rky * W[2] - rkz * W[1], rCy = rkz * W[0] - rkx * W[2], rCz = rkx * W[1] - rky * W[0];
         const R s = W[3] + W[4], t = W[3] - W[4];
         const R as = al * s, act = alc * t;
         U[0] = Wk + as;
-        U[1] = u * U[0] + (rho * Cx + act * kx);
-        U[2] = v * U[0] + (rho * Cy + act * ky);
-        U[3] = w * U[0] + (rho * Cz + act * kz);
-        U[4] = half_uu * Wk + rho * (u * Cx + v * Cy + w * Cz) + as * H + acth * t;
+        U[1] = u * U[0] + (rCx + act * kx);
+        U[2] = v * U[0] + (rCy + act * ky);
+        U[3] = w * U[0] + (rCz + act * kz);
+        U[4] = half_uu * Wk + (u * rCx + v * rCy + w * rCz) + as * H + acth * t;
     }
 };
 
@@ -779,7 +783,8 @@ __device__ __forceinline__ float hneg(float x) {
     return __int_as_float(b & (b >> 31));
 }
 
-// Steger-Warming split flux along metric (kx, ky, kz) * mm; POS selects F+.
+// Steger-Warming split flux along metric (kx, ky, kz) * |m|, with mmg =
+// |m| / (2 gamma); POS selects F+.
 //   F = rho |m| / (2 gamma) [M, u M + c kx D, v M + c ky D, w M + c kz D,
 //                            (gamma-1) l1 |u|^2 + (l4+l5) H + c theta D]
 //   with l = lambda^+- of (theta, theta + c, theta - c) (the factor |m| > 0
@@ -787,11 +792,14 @@ __device__ __forceinline__ float hneg(float x) {
 //   H = |u|^2/2 + c^2/(gamma-1): the energy row's (|u|^2+c^2)/2 and
 //   (3-gamma) c^2 / (2 (gamma-1)) terms of (l4+l5) sum to H.
 template <class R, bool POS>
-__device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R irho, R kx, R ky, R kz, R mm, R F[5]) {
+__device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R irho, R kx, R ky, R kz, R mmg, R F[5]) {
     const R u = q[1] * irho, v = q[2] * irho, w = q[3] * irho;
     const R uu = u * u + v * v + w * w;
-    const R p = gs.gm1 * (q[4] - R(0.5) * q[0] * uu);
-    const R c2 = gs.gamma * p * irho;
+    // t = E/rho - |u|^2/2 = p / ((gamma-1) rho): c^2 = gamma (gamma-1) t and
+    // H = E/rho + (gamma-1) t, without forming p
+    const R e = q[4] * irho;
+    const R t = e - R(0.5) * uu;
+    const R c2 = gs.g_gm1 * t;
     const R c = c2 * hrsqrt(c2);
     const R th = kx * u + ky * v + kz * w;
     R l1 = th, l4 = th + c, l5 = th - c;
@@ -804,11 +812,11 @@ __device__ __forceinline__ void sw_flux(const GasR<R>& gs, const R q[5], R irho,
         l4 = hneg(l4);
         l5 = hneg(l5);
     }
-    const R a = q[0] * mm * gs.inv_2gamma;
+    const R a = q[0] * mmg;
     const R S45 = l4 + l5, D45 = l4 - l5;
     const R aM = a * (gs.two_gm1 * l1 + S45);
     const R acD = a * (c * D45);
-    const R H = R(0.5) * uu + c2 * gs.inv_gm1;
+    const R H = e + gs.gm1 * t;
     F[0] = aM;
     F[1] = u * aM + kx * acD;
     F[2] = v * aM + ky * acD;
@@ -831,9 +839,10 @@ __device__ __forceinline__ void face_flux(const GasR<R>& gs, const R ql[5], cons
         il = hrcp(ql[0]);
         ir = hrcp(qr[0]);
     }
+    const R mmg = mm * gs.inv_2gamma;   // |m| / (2 gamma), shared by the two sides
     R Fp[5], Fm[5];
-    sw_flux<R, true>(gs, ql, il, kx, ky, kz, mm, Fp);
-    sw_flux<R, false>(gs, qr, ir, kx, ky, kz, mm, Fm);
+    sw_flux<R, true>(gs, ql, il, kx, ky, kz, mmg, Fp);
+    sw_flux<R, false>(gs, qr, ir, kx, ky, kz, mmg, Fm);
 #pragma unroll
     for (int k = 0; k < 5; ++k) h[k] = Fp[k] + Fm[k];
 }
