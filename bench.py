@@ -66,12 +66,12 @@ def stage_bytes_per_node(precision):
 # stages' launches (profiles/traffic_tgv192.md gives the command).  Scaled
 # to the benchmark's workload by its node count; null when the kernel
 # sources differ from the captured ones.
-TRAFFIC_SOURCES_SHA = "24a4b56c0f6d7a86"
+TRAFFIC_SOURCES_SHA = "c3135e334f6465f9"
 TRAFFIC_PER_NODE = {
     ("mixed", "prep"): 21.1, ("mixed", "stress"): 100.9, ("mixed", "flux_xi"): 97.7,
-    ("mixed", "flux_eta"): 115.6, ("mixed", "flux_zeta"): 145.8, ("mixed", "rk_stage"): 185.2,
-    ("fp64", "prep"): 196.8, ("fp64", "stress"): 211.9, ("fp64", "flux_xi"): 351.7,
-    ("fp64", "flux_eta"): 405.0, ("fp64", "flux_zeta_rk"): 444.2,
+    ("mixed", "flux_eta"): 115.6, ("mixed", "flux_zeta"): 144.7, ("mixed", "rk_stage"): 185.2,
+    ("fp64", "prep"): 196.8, ("fp64", "stress"): 211.8, ("fp64", "flux_xi"): 352.0,
+    ("fp64", "flux_eta"): 404.9, ("fp64", "flux_zeta_rk"): 444.0,
 }
 
 # Algorithmic work per node and RK stage besides the three sweeps: the
