@@ -63,9 +63,14 @@ def stage_bytes_per_node(precision):
 # of one launch of each stage kernel, from one ncu capture of the kernels
 # whose sources hash to TRAFFIC_SOURCES_SHA: the 192^3 Taylor-Green block
 # (7,077,888 nodes) with the fixed tiles, the mean over the three RK
-# stages' launches (profiles/traffic_tgv192.md gives the command).  Scaled
-# to the benchmark's workload by its node count; null when the kernel
-# sources differ from the captured ones.
+# stages' launches of the second warm-up step:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:'k_flux|k_grad|k_prep|k_rk_stage'
+#       -s 22 -c 18 (mixed; FP64: -s 15 -c 15) --csv
+#       python bench.py --workload tgv192 --steps 1 --warmup 3 --no-cpu-baseline
+#       --no-autotune --forms mixed (or fp64)
+# Scaled to the benchmark's workload by its node count; null when the
+# kernel sources differ from the captured ones.
 TRAFFIC_SOURCES_SHA = "c3135e334f6465f9"
 TRAFFIC_PER_NODE = {
     ("mixed", "prep"): 21.1, ("mixed", "stress"): 100.9, ("mixed", "flux_xi"): 97.7,
